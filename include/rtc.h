@@ -1,0 +1,276 @@
+/*
+ * rtc.h - C ABI of the GB300 adaptive-optics real-time-control hot path.
+ *
+ * The path follows the per-frame pipeline of Jenkins, Basden & Myers,
+ * "A many-core CPU prototype of an MCAO and LTAO RTC for ELT-scale
+ * instruments" (arXiv 1903.01852):
+ *
+ *   WFS pixels (streamed in row chunks, Section 2.1-2.2)
+ *     -> calibration (dark subtraction, flat field, threshold; Section 2.2)
+ *     -> Shack-Hartmann centre-of-gravity or pyramid quad-difference slopes
+ *        (Fig. wfs_slopes, Section 2.2)
+ *     -> reconstruction matrix-vector multiply, one partial per column block
+ *        (Section 2.3; per-WFS partial DM commands summed by a master, Section 3)
+ *     -> implicit pseudo-open-loop control term + leaky integrator
+ *        (Section 3.4) -> DM commands, tagged with the camera frame number
+ *        (Section 3, Fig. mcaoltao_test).
+ *
+ * Conventions for every entry point:
+ *   - Sizes are element counts unless a name ends in "pitch" (bytes).
+ *   - Every input array is owned by the caller and is copied (or, for the
+ *     device-resident frame entry point, read in place) before the call
+ *     returns its status; the library keeps no caller pointer after the call,
+ *     except as stated for rtc_submit_pixels / rtc_process_frame.
+ *   - Calls return an int status: RTC_OK (0) or a negative RTC_E* code.
+ *     No C++ exception crosses the ABI.  The text of the last failure is
+ *     available from rtc_last_error().
+ *   - One thread submits to a loop; any thread may call rtc_get_commands,
+ *     rtc_get_telemetry and rtc_get_timing.
+ *
+ * Slope order (the paper does not fix one): interleaved (x, y) per valid
+ * unit, units in row-major order of the subaperture grid (SH) or of the pupil
+ * (pyramid), WFS after WFS in the order given at creation.  Column j of the
+ * control matrix multiplies slope j.
+ */
+#ifndef RTC_H
+#define RTC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define RTC_OK         0
+#define RTC_EINVAL    -1  /* bad argument: size, pointer, enum, alignment, NaN/Inf in a map */
+#define RTC_ENOMEM    -2  /* device or page-locked host memory could not be had (HBM admission) */
+#define RTC_ETIMEDOUT -3  /* a wait ran out before the result was ready */
+#define RTC_EORDER    -4  /* chunk rejected: frame id not increasing, or rows not contiguous */
+#define RTC_EDROPPED  -5  /* chunk accepted, but the previous frame was incomplete and was dropped */
+#define RTC_ECUDA     -6  /* a CUDA runtime call failed; the loop should be destroyed */
+#define RTC_ENOENT    -7  /* the requested frame is no longer (or not yet) in the ring */
+
+/* ---- enumerations ---------------------------------------------------- */
+#define RTC_WFS_SH       0  /* Shack-Hartmann: centre of gravity per subaperture */
+#define RTC_WFS_PYRAMID  1  /* pyramid: normalised quad difference per pupil pixel */
+
+#define RTC_F32   0         /* IEEE binary32 */
+#define RTC_BF16  1         /* bfloat16 codes (uint16 bit patterns) */
+#define RTC_E4M3  2         /* FP8 E4M3 (finite-only, max 448) codes (uint8 bit patterns) */
+
+#define RTC_THRESH_SUBTRACT 0  /* t = max(c - T, 0) */
+#define RTC_THRESH_CLIP     1  /* t = c if c > T else 0 */
+
+#define RTC_FLAG_TIMING     1u /* record per-stage CUDA events (rtc_get_timing) */
+#define RTC_FLAG_TELEMETRY  2u /* copy slopes of every frame to the page-locked ring */
+
+#define RTC_MAX_WFS 16
+
+/* ---- creation-time descriptions ------------------------------------- */
+
+/* One wavefront sensor.  Pixel frames are uint16, row-major, height x width.
+ * SH: a grid of nsuby x nsubx subapertures of npx x npx pixels whose top-left
+ * pixel is (ox, oy); the grid must lie inside the frame.
+ * Pyramid: four pupil images of pupil x pupil pixels with top-left pixels
+ * (qx[k], qy[k]) for k = A (top-left), B (top-right), C (bottom-left),
+ * D (bottom-right); each must lie inside the frame.
+ * valid: host uint8, row-major, nsuby x nsubx (SH) or pupil x pupil (pyramid);
+ * non-zero marks a valid unit; NULL means every unit is valid.
+ * nblocks: number of reconstruction column blocks this WFS's slopes are split
+ * into, by whole slope rows (subaperture rows or pupil rows), as evenly as
+ * possible; a block's MVM starts as soon as its pixel rows have arrived
+ * (Section 2.2: centroiding starts when a row of subapertures is complete).
+ * 1 <= nblocks <= number of slope rows. */
+typedef struct rtc_wfs {
+    int32_t kind;
+    int32_t width, height;
+    int32_t nsubx, nsuby, npx, ox, oy;   /* SH only */
+    int32_t pupil, qx[4], qy[4];         /* pyramid only */
+    const uint8_t* valid;
+    int32_t nblocks;
+} rtc_wfs;
+
+/* The loop's sensors and run-time options. */
+typedef struct rtc_geometry {
+    int32_t nwfs;                /* 1..RTC_MAX_WFS */
+    const rtc_wfs* wfs;          /* host array of nwfs */
+    int32_t device;              /* CUDA device ordinal */
+    uint32_t flags;              /* RTC_FLAG_* */
+    int32_t ring;                /* depth of the page-locked command/telemetry ring, >= 2 */
+} rtc_geometry;
+
+/* Pixel calibration (Section 2.2): c = (raw - dark) * flat, then the threshold.
+ * Each map is host float32, row-major height x width of its WFS.
+ * dark / flat: arrays of nwfs pointers; the array or an entry may be NULL
+ * (dark 0, flat 1).  threshold: nwfs values >= 0 or NULL (0).  thresh_mode:
+ * nwfs RTC_THRESH_* values or NULL (SUBTRACT).  ref_slopes: ns reference
+ * slopes subtracted from the measured ones, or NULL.
+ * Whether a pixel is lit (t > 0) is decided on the float32 value
+ * fl(fl(raw - dark) * flat) compared with T. */
+typedef struct rtc_calib {
+    const float* const* dark;
+    const float* const* flat;
+    const float* threshold;
+    const int32_t* thresh_mode;
+    const float* ref_slopes;
+} rtc_calib;
+
+/* Control (reconstruction) matrix M, na x ns, host, row-major, element type
+ * dtype (RTC_F32 floats, RTC_BF16 uint16 codes, RTC_E4M3 uint8 codes).
+ * row_scale: host float32[na] multiplying each row (required for BF16/E4M3
+ * codes produced by rtc_quantize_rows; optional for F32), or NULL.
+ * ns must equal the loop's slope count.  The matrix is re-laid out into
+ * column blocks in device memory; the caller's copy is not kept. */
+typedef struct rtc_cmat {
+    int32_t na, ns;
+    int32_t dtype;
+    const void* data;
+    const float* row_scale;
+} rtc_cmat;
+
+/* Control law with implicit POLC (Section 3.4):
+ *   a_k = (1 - leak) a_{k-1} + gain (M s_k + q_{k-1}),  q_k = P a_k,
+ * then the optional clip to [amin, amax].  q_k is computed after frame k's
+ * commands are ready, for frame k+1, off the latency path.
+ * P: host row-major na x na of element type dtype with optional row_scale,
+ * or NULL for a plain leaky integrator (q = 0).  a0: host float32[na]
+ * initial commands, or NULL for zeros. */
+typedef struct rtc_polc {
+    const void* P;
+    int32_t dtype;
+    const float* row_scale;
+    float gain, leak;
+    const float* a0;
+    int32_t clip;
+    float amin, amax;
+} rtc_polc;
+
+typedef struct rtc_loop rtc_loop;   /* opaque */
+
+/* Validate the description, copy every map and matrix into device memory of
+ * geometry->device (admission fails with RTC_ENOMEM when they do not fit),
+ * build the slope-row and column-block plans, allocate the page-locked
+ * command ring and the CUDA streams and events.  On success *out is a new
+ * loop; on failure *out is NULL and rtc_last_error(NULL) has the reason. */
+int rtc_create(const rtc_geometry* geometry, const rtc_calib* calib,
+               const rtc_cmat* cmat, const rtc_polc* polc, rtc_loop** out);
+
+/* Wait for all work of the loop, then release everything it holds.
+ * NULL is accepted.  The loop must not be used afterwards. */
+int rtc_destroy(rtc_loop* loop);
+
+/* ---- per-frame entry points ----------------------------------------- */
+
+/* A run of whole pixel rows [row_begin, row_end) of one WFS frame.
+ * px points at the first pixel of row_begin, in host memory (pageable or
+ * page-locked) or device memory; rows are pitch bytes apart (pitch >=
+ * 2*width).  frame_id is the camera's frame number (Section 3: it is
+ * carried through to the DM command). */
+typedef struct rtc_chunk {
+    uint64_t frame_id;
+    int32_t wfs;
+    int32_t row_begin, row_end;
+    const uint16_t* px;
+    size_t pitch;
+} rtc_chunk;
+
+/* Pixel-stream ingest (Section 2.1-2.2).  Enqueues the copy of the rows into
+ * the loop's frame buffer, the calibration + slopes of every slope row those
+ * rows complete, and the MVM of every column block they complete; when the
+ * last row of the last WFS of the frame arrives, also the finalisation
+ * (partial sums + POLC term + integrator) that writes the commands, then the
+ * POLC product for the next frame.  Returns without waiting for the GPU.
+ * Rows of one WFS must arrive in order without gaps; WFS may interleave.
+ * A chunk of a new (larger) frame_id while the current frame is incomplete
+ * drops the current frame (its commands are never produced, the integrator
+ * state is unchanged) and returns RTC_EDROPPED with the chunk accepted.
+ * A smaller or repeated frame_id of a completed frame, or non-contiguous
+ * rows, return RTC_EORDER and change nothing.
+ * px from pageable memory may be reused when the call returns; px in
+ * page-locked or device memory must stay unchanged until rtc_get_commands
+ * has returned this frame. */
+int rtc_submit_pixels(rtc_loop* loop, const rtc_chunk* chunk);
+
+/* Whole-frame entry point for frames already resident in device memory
+ * (e.g. written there by a frame grabber): px[w] is a device pointer to WFS
+ * w's frame (16-byte aligned), pitch[w] its row pitch in bytes (a multiple
+ * of 16, >= 2*width rounded up to 16).  The slope kernels read the frames in
+ * place; they must stay unchanged until rtc_get_commands returns this frame.
+ * Otherwise behaves like submitting every row of every WFS at once. */
+int rtc_process_frame(rtc_loop* loop, uint64_t frame_id,
+                      const uint16_t* const* px, const size_t* pitch);
+
+/* Wait (busy-polling, up to timeout_us microseconds; <0 waits forever) for
+ * the oldest frame whose pixels are all submitted and whose commands have not
+ * yet been returned, then copy its na commands to out (host) and its frame
+ * id to *frame_id.  RTC_ETIMEDOUT leaves that frame queued.  The ring keeps
+ * the last `ring` frames; older unread ones are discarded. */
+int rtc_get_commands(rtc_loop* loop, float* out, size_t n, uint64_t* frame_id,
+                     int64_t timeout_us);
+
+/* Telemetry (Section 3.3): copy the slopes (ns, measured minus reference)
+ * and commands (na) of frame_id, if it is still in the ring, to host
+ * buffers; either pointer may be NULL.  Needs RTC_FLAG_TELEMETRY for slopes.
+ * Waits up to timeout_us for that frame's GPU work. */
+int rtc_get_telemetry(rtc_loop* loop, uint64_t frame_id, float* slopes, size_t ns,
+                      float* cmds, size_t na, int64_t timeout_us);
+
+/* Device times of one frame's stages, from CUDA events on the loop's stream
+ * (needs RTC_FLAG_TIMING).  For rtc_process_frame: slopes, MVM, finalise
+ * and POLC kernels, and latency = start of the slope kernel to the end of
+ * the finalise kernel.  For chunked frames: stage times of the last chunk,
+ * and latency = start of the last chunk's copy to the end of finalise. */
+typedef struct rtc_timing {
+    uint64_t frame_id;
+    float slopes_us, mvm_us, final_us, polc_us;
+    float latency_us, frame_us;  /* frame_us: first submitted work to end of finalise */
+} rtc_timing;
+int rtc_get_timing(rtc_loop* loop, uint64_t frame_id, rtc_timing* out, int64_t timeout_us);
+
+/* ---- state and introspection ---------------------------------------- */
+
+/* Wait for queued work, then copy the integrator state a (na floats) out. */
+int rtc_get_state(rtc_loop* loop, float* a, size_t na);
+/* Wait for queued work, then set a and recompute q = P a (checkpoint resume). */
+int rtc_set_state(rtc_loop* loop, const float* a, size_t na);
+/* Wait for all queued work of the loop. */
+int rtc_sync(rtc_loop* loop);
+
+/* The loop's CUDA stream (a cudaStream_t) in *stream, so a caller can order
+ * its own work or timing events after the loop's; the loop keeps ownership. */
+int rtc_get_stream(rtc_loop* loop, void** stream);
+
+typedef struct rtc_info {
+    int32_t na, ns, nwfs, nblocks, nrows;
+    int32_t m_dtype, p_dtype;
+    uint64_t m_bytes;          /* bytes of the stored matrix streamed per frame (incl. padding) */
+    uint64_t p_bytes;          /* bytes of the stored POLC matrix (0 without POLC) */
+    uint64_t pixel_bytes;      /* raw + calibration bytes read per frame by the slope kernels */
+    uint64_t device_bytes;     /* device memory held by the loop */
+    uint64_t frames_done, frames_dropped, frames_overrun;
+} rtc_info;
+int rtc_get_info(rtc_loop* loop, rtc_info* out);
+
+/* Text of the last failure on this loop, or (loop NULL) of the last failed
+ * rtc_create / stateless call on the calling thread.  Never NULL. */
+const char* rtc_last_error(const rtc_loop* loop);
+
+/* ---- stateless device operations ------------------------------------ */
+
+/* Per-row scaled quantisation of a float32 matrix in device memory, for
+ * storing M or P in BF16 or E4M3 (halving / quartering the bytes the MVM
+ * streams).  scale_r = max_j |M_rj| (BF16) or max_j |M_rj| / 448 (E4M3),
+ * 1 for an all-zero row; code_rj = round-to-nearest-even of fl(M_rj/scale_r),
+ * saturating at +-448 for E4M3.  M: device float32, row r at M + r*ld.
+ * codes: device, row-major na x ns (uint16 for BF16, uint8 for E4M3).
+ * scale: device float32[na].  stream: a cudaStream_t or NULL (legacy
+ * default stream).  Asynchronous; returns RTC_EINVAL on bad arguments. */
+int rtc_quantize_rows(int32_t dtype, int32_t na, int32_t ns, const float* M, size_t ld,
+                      void* codes, float* scale, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTC_H */

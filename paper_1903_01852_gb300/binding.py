@@ -1,0 +1,318 @@
+"""ctypes binding of ``librtc.so`` (include/rtc.h): argument marshalling only.
+
+Every step of the hot path runs in the library's CUDA kernels; this module
+only builds the C structs from a configuration dict, passes pointers (numpy
+arrays for host data, torch tensors for device data) and turns status codes
+into exceptions.  There is no fallback: if the library is missing or cannot
+be loaded, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librtc.so")
+
+RTC_OK, RTC_EINVAL, RTC_ENOMEM, RTC_ETIMEDOUT = 0, -1, -2, -3
+RTC_EORDER, RTC_EDROPPED, RTC_ECUDA, RTC_ENOENT = -4, -5, -6, -7
+RTC_WFS_SH, RTC_WFS_PYRAMID = 0, 1
+RTC_F32, RTC_BF16, RTC_E4M3 = 0, 1, 2
+RTC_THRESH_SUBTRACT, RTC_THRESH_CLIP = 0, 1
+RTC_FLAG_TIMING, RTC_FLAG_TELEMETRY = 1, 2
+RTC_MAX_WFS = 16
+DTYPES = {"f32": RTC_F32, "bf16": RTC_BF16, "e4m3": RTC_E4M3}
+CODE_NP = {RTC_F32: np.float32, RTC_BF16: np.uint16, RTC_E4M3: np.uint8}
+STATUS = {0: "RTC_OK", -1: "RTC_EINVAL", -2: "RTC_ENOMEM", -3: "RTC_ETIMEDOUT", -4: "RTC_EORDER",
+          -5: "RTC_EDROPPED", -6: "RTC_ECUDA", -7: "RTC_ENOENT"}
+
+f32p = C.POINTER(C.c_float)
+
+
+class rtc_wfs(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("width", C.c_int32), ("height", C.c_int32),
+                ("nsubx", C.c_int32), ("nsuby", C.c_int32), ("npx", C.c_int32), ("ox", C.c_int32),
+                ("oy", C.c_int32), ("pupil", C.c_int32), ("qx", C.c_int32 * 4), ("qy", C.c_int32 * 4),
+                ("valid", C.POINTER(C.c_uint8)), ("nblocks", C.c_int32)]
+
+
+class rtc_geometry(C.Structure):
+    _fields_ = [("nwfs", C.c_int32), ("wfs", C.POINTER(rtc_wfs)), ("device", C.c_int32),
+                ("flags", C.c_uint32), ("ring", C.c_int32)]
+
+
+class rtc_calib(C.Structure):
+    _fields_ = [("dark", C.POINTER(f32p)), ("flat", C.POINTER(f32p)), ("threshold", f32p),
+                ("thresh_mode", C.POINTER(C.c_int32)), ("ref_slopes", f32p)]
+
+
+class rtc_cmat(C.Structure):
+    _fields_ = [("na", C.c_int32), ("ns", C.c_int32), ("dtype", C.c_int32), ("data", C.c_void_p),
+                ("row_scale", f32p)]
+
+
+class rtc_polc(C.Structure):
+    _fields_ = [("P", C.c_void_p), ("dtype", C.c_int32), ("row_scale", f32p), ("gain", C.c_float),
+                ("leak", C.c_float), ("a0", f32p), ("clip", C.c_int32), ("amin", C.c_float),
+                ("amax", C.c_float)]
+
+
+class rtc_chunk(C.Structure):
+    _fields_ = [("frame_id", C.c_uint64), ("wfs", C.c_int32), ("row_begin", C.c_int32),
+                ("row_end", C.c_int32), ("px", C.c_void_p), ("pitch", C.c_size_t)]
+
+
+class rtc_timing(C.Structure):
+    _fields_ = [("frame_id", C.c_uint64), ("slopes_us", C.c_float), ("mvm_us", C.c_float),
+                ("final_us", C.c_float), ("polc_us", C.c_float), ("latency_us", C.c_float),
+                ("frame_us", C.c_float)]
+
+
+class rtc_info(C.Structure):
+    _fields_ = [("na", C.c_int32), ("ns", C.c_int32), ("nwfs", C.c_int32), ("nblocks", C.c_int32),
+                ("nrows", C.c_int32), ("m_dtype", C.c_int32), ("p_dtype", C.c_int32),
+                ("m_bytes", C.c_uint64), ("p_bytes", C.c_uint64), ("pixel_bytes", C.c_uint64),
+                ("device_bytes", C.c_uint64), ("frames_done", C.c_uint64), ("frames_dropped", C.c_uint64),
+                ("frames_overrun", C.c_uint64)]
+
+
+# (name, restype, argtypes) of every entry point declared in include/rtc.h
+SIGNATURES = [
+    ("rtc_create", C.c_int, [C.POINTER(rtc_geometry), C.POINTER(rtc_calib), C.POINTER(rtc_cmat),
+                             C.POINTER(rtc_polc), C.POINTER(C.c_void_p)]),
+    ("rtc_destroy", C.c_int, [C.c_void_p]),
+    ("rtc_submit_pixels", C.c_int, [C.c_void_p, C.POINTER(rtc_chunk)]),
+    ("rtc_process_frame", C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(C.c_void_p), C.POINTER(C.c_size_t)]),
+    ("rtc_get_commands", C.c_int, [C.c_void_p, f32p, C.c_size_t, C.POINTER(C.c_uint64), C.c_int64]),
+    ("rtc_get_telemetry", C.c_int, [C.c_void_p, C.c_uint64, f32p, C.c_size_t, f32p, C.c_size_t, C.c_int64]),
+    ("rtc_get_timing", C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(rtc_timing), C.c_int64]),
+    ("rtc_get_state", C.c_int, [C.c_void_p, f32p, C.c_size_t]),
+    ("rtc_set_state", C.c_int, [C.c_void_p, f32p, C.c_size_t]),
+    ("rtc_sync", C.c_int, [C.c_void_p]),
+    ("rtc_get_stream", C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
+    ("rtc_get_info", C.c_int, [C.c_void_p, C.POINTER(rtc_info)]),
+    ("rtc_last_error", C.c_char_p, [C.c_void_p]),
+    ("rtc_quantize_rows", C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_size_t, C.c_void_p,
+                                    C.c_void_p, C.c_void_p]),
+]
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_1903_01852_gb300.build`")
+    lib = C.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = load()
+
+
+class RtcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _err(loop_ptr=None):
+    return lib.rtc_last_error(loop_ptr).decode(errors="replace")
+
+
+def _check(rc, loop_ptr=None, allow=()):
+    if rc != RTC_OK and rc not in allow:
+        raise RtcError(rc, _err(loop_ptr))
+    return rc
+
+
+def _fptr(a):
+    return None if a is None else a.ctypes.data_as(f32p)
+
+
+def _f32(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _ptr(x):
+    """Address of a numpy array or torch tensor (host or device)."""
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def _pitch(x):
+    """Row pitch in bytes of a 2-D uint16 array or tensor."""
+    if hasattr(x, "stride") and callable(x.stride):
+        return x.stride(0) * x.element_size()
+    return x.strides[0]
+
+
+class Loop:
+    """One AO loop on one GPU, built from a configuration dict (see synth)."""
+
+    def __init__(self, cfg, device=0, timing=False, telemetry=False, ring=4):
+        self.cfg = cfg
+        self.na = int(cfg["na"])
+        wl = cfg["wfs"]
+        if len(wl) > RTC_MAX_WFS:
+            raise ValueError("too many WFS")
+        keep = []   # host arrays that must outlive rtc_create
+        warr = (rtc_wfs * len(wl))()
+        darks = (f32p * len(wl))()
+        flats = (f32p * len(wl))()
+        thr = np.array([w.get("threshold", 0.0) for w in wl], np.float32)
+        mode = np.array([RTC_THRESH_CLIP if w.get("thresh_mode") == "clip" else RTC_THRESH_SUBTRACT for w in wl],
+                        np.int32)
+        for k, w in enumerate(wl):
+            s = warr[k]
+            s.kind = RTC_WFS_SH if w["kind"] == "sh" else RTC_WFS_PYRAMID
+            s.width, s.height = w["width"], w["height"]
+            if w["kind"] == "sh":
+                s.nsubx, s.nsuby, s.npx, s.ox, s.oy = w["nsubx"], w["nsuby"], w["npx"], w["ox"], w["oy"]
+            else:
+                s.pupil = w["pupil"]
+                for q in range(4):
+                    s.qx[q], s.qy[q] = w["qx"][q], w["qy"][q]
+            v = np.ascontiguousarray(w["valid"], dtype=np.uint8)
+            keep.append(v)
+            s.valid = v.ctypes.data_as(C.POINTER(C.c_uint8))
+            s.nblocks = int(w.get("nblocks", 1))
+            d, f = _f32(w.get("dark")), _f32(w.get("flat"))
+            keep += [d, f]
+            darks[k] = _fptr(d)
+            flats[k] = _fptr(f)
+        flags = (RTC_FLAG_TIMING if timing else 0) | (RTC_FLAG_TELEMETRY if telemetry else 0)
+        geo = rtc_geometry(len(wl), warr, device, flags, ring)
+        ref = _f32(cfg.get("ref_slopes"))
+        cal = rtc_calib(darks, flats, thr.ctypes.data_as(f32p), mode.ctypes.data_as(C.POINTER(C.c_int32)), _fptr(ref))
+        mdt = DTYPES[cfg.get("M_dtype", "f32")]
+        M = np.ascontiguousarray(cfg["M"], dtype=CODE_NP[mdt])
+        ms = _f32(cfg.get("M_scale"))
+        cm = rtc_cmat(M.shape[0], M.shape[1], mdt, M.ctypes.data, _fptr(ms))
+        P = cfg.get("P")
+        pdt = DTYPES[cfg.get("P_dtype", "f32")]
+        Pa = None if P is None else np.ascontiguousarray(P, dtype=CODE_NP[pdt])
+        ps = _f32(cfg.get("P_scale"))
+        a0 = _f32(cfg.get("a0"))
+        clip = cfg.get("clip")
+        pol = rtc_polc(None if Pa is None else Pa.ctypes.data, pdt, _fptr(ps), float(cfg["gain"]), float(cfg["leak"]),
+                       _fptr(a0), 1 if clip else 0, float(clip[0]) if clip else 0.0, float(clip[1]) if clip else 0.0)
+        h = C.c_void_p()
+        _check(lib.rtc_create(C.byref(geo), C.byref(cal), C.byref(cm), C.byref(pol), C.byref(h)))
+        self._h = h
+        inf = self.info()
+        self.ns = inf["ns"]
+        self._cmd = np.empty(self.na, np.float32)
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib.rtc_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- per frame --------------------------------------------------------
+    def submit(self, frame_id, wfs, row_begin, row_end, px, pitch=None):
+        """Submit rows [row_begin, row_end) of WFS ``wfs``; ``px`` is a 2-D uint16 array/tensor
+        whose first row is row_begin.  Returns RTC_OK or RTC_EDROPPED."""
+        ch = rtc_chunk(frame_id, wfs, row_begin, row_end, _ptr(px), _pitch(px) if pitch is None else pitch)
+        return _check(lib.rtc_submit_pixels(self._h, C.byref(ch)), self._h, allow=(RTC_EDROPPED,))
+
+    def submit_frame(self, frame_id, frames, plans=None):
+        """Submit a whole frame as row chunks; ``plans[w]`` lists (row_begin, row_end) for WFS w
+        (default: one chunk per WFS).  WFS are interleaved chunk by chunk, as parallel cameras
+        would deliver them."""
+        status = RTC_OK
+        plans = plans or [[(0, f.shape[0])] for f in frames]
+        n = max(len(p) for p in plans)
+        for c in range(n):
+            for w, plan in enumerate(plans):
+                if c < len(plan):
+                    r0, r1 = plan[c]
+                    rc = self.submit(frame_id, w, r0, r1, frames[w][r0:r1])
+                    status = rc if rc != RTC_OK else status
+        return status
+
+    def process_frame(self, frame_id, dev_frames):
+        """Whole frame from device-resident uint16 tensors (one per WFS)."""
+        n = len(dev_frames)
+        px = (C.c_void_p * n)(*[t.data_ptr() for t in dev_frames])
+        pitch = (C.c_size_t * n)(*[t.stride(0) * t.element_size() for t in dev_frames])
+        return _check(lib.rtc_process_frame(self._h, frame_id, px, pitch), self._h, allow=(RTC_EDROPPED,))
+
+    def get_commands(self, timeout_us=-1, out=None):
+        out = self._cmd.copy() if out is None else out
+        fid = C.c_uint64()
+        rc = lib.rtc_get_commands(self._h, out.ctypes.data_as(f32p), self.na, C.byref(fid), int(timeout_us))
+        if rc == RTC_ETIMEDOUT:
+            raise TimeoutError(_err(self._h))
+        _check(rc, self._h)
+        return fid.value, out
+
+    def get_telemetry(self, frame_id, timeout_us=-1):
+        s = np.empty(self.ns, np.float32)
+        a = np.empty(self.na, np.float32)
+        _check(lib.rtc_get_telemetry(self._h, frame_id, s.ctypes.data_as(f32p), self.ns,
+                                     a.ctypes.data_as(f32p), self.na, int(timeout_us)), self._h)
+        return s, a
+
+    def get_timing(self, frame_id, timeout_us=-1):
+        t = rtc_timing()
+        _check(lib.rtc_get_timing(self._h, frame_id, C.byref(t), int(timeout_us)), self._h)
+        return {k: getattr(t, k) for k, _ in rtc_timing._fields_}
+
+    # -- state ----------------------------------------------------------------
+    def get_state(self):
+        a = np.empty(self.na, np.float32)
+        _check(lib.rtc_get_state(self._h, a.ctypes.data_as(f32p), self.na), self._h)
+        return a
+
+    def set_state(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        _check(lib.rtc_set_state(self._h, a.ctypes.data_as(f32p), self.na), self._h)
+
+    def sync(self):
+        _check(lib.rtc_sync(self._h), self._h)
+
+    def stream(self):
+        """The loop's cudaStream_t as an integer handle."""
+        h = C.c_void_p()
+        _check(lib.rtc_get_stream(self._h, C.byref(h)), self._h)
+        return h.value or 0
+
+    def info(self):
+        i = rtc_info()
+        _check(lib.rtc_get_info(self._h, C.byref(i)), self._h)
+        return {k: getattr(i, k) for k, _ in rtc_info._fields_}
+
+    @property
+    def last_error(self):
+        return _err(self._h)
+
+
+def quantize_rows(M, fmt, stream=None):
+    """Per-row scaled BF16 / E4M3 quantisation of a float32 CUDA tensor [na, ns]
+    (rtc_quantize_rows).  Returns (codes, scale) CUDA tensors."""
+    import torch
+    dt = DTYPES[fmt]
+    na, ns = M.shape
+    codes = torch.empty((na, ns), dtype=torch.int16 if dt == RTC_BF16 else torch.uint8, device=M.device)
+    scale = torch.empty(na, dtype=torch.float32, device=M.device)
+    st = stream if stream is not None else torch.cuda.current_stream(M.device).cuda_stream
+    _check(lib.rtc_quantize_rows(dt, na, ns, M.data_ptr(), M.stride(0), codes.data_ptr(), scale.data_ptr(), st))
+    return codes, scale

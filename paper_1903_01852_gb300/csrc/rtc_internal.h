@@ -1,0 +1,94 @@
+// Internal device-side plans and kernel launchers of the AO RTC library.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/rtc.h"
+
+namespace rtc {
+
+constexpr int kMaxWfs = RTC_MAX_WFS;
+constexpr int kSlopeThreads = 256;    // threads per slope-row CTA
+constexpr int kGemvWarps = 8;         // warps per GEMV CTA
+
+// Per-WFS constants read by the slope kernel.
+struct WfsDev {
+    int kind;                 // RTC_WFS_SH or RTC_WFS_PYRAMID
+    int width, height;
+    int npx, nsubx, nsuby, ox, oy;
+    int pupil, qx[4], qy[4];
+    float threshold;
+    int thresh_mode;
+    const float* dark;        // device, calib_pitch floats per row
+    const float* flat;
+    int calib_pitch;          // floats per calibration-map row (multiple of 4)
+    int sh_groups;            // SH: row groups per CTA in the column-sum phase
+};
+
+// One slope row: a subaperture row (SH) or a pupil row (pyramid).
+struct SlopeRow {
+    int wfs;
+    int row;                  // row index within its WFS
+    int unit0;                // first entry of this row in the unit x-list
+    int nunits;               // valid units in this row
+    int s_pad;                // padded slope-buffer index of the row's first slope
+    int s_compact;            // compact slope index of the row's first slope
+};
+
+// Frame pointers for one launch; pitch in uint16 elements.
+struct FramePtrs {
+    const uint16_t* px[kMaxWfs];
+    long long pitch[kMaxWfs];
+};
+
+// One reconstruction column block, stored as a dense [na][pitch] sub-matrix.
+struct BlockDev {
+    long long m_off;          // element offset of the sub-matrix
+    int x_off;                // padded input-vector index of the block's first column
+    int ncols;                // true columns
+    int pitch;                // stored columns (multiple of 16 bytes / element size)
+    int c0;                   // compact index of the block's first column
+};
+
+size_t dtype_size(int dtype);
+int elems_per_16B(int dtype);
+
+// Opt the slope kernel in to more than 48 KB of dynamic shared memory when needed.
+cudaError_t configure_slopes(int smem_bytes);
+
+// Slope kernel over table rows [row0, row0 + nrows).
+cudaError_t launch_slopes(const SlopeRow* rows, int row0, int nrows, const WfsDev* wfs,
+                          const FramePtrs& fp, const uint16_t* xlist, const float* ref,
+                          float* s_pad, int smem_bytes, cudaStream_t st);
+
+// GEMV over blocks [b0, b0 + nb): out[b * out_stride + r] = sum_j M_b[r][j] x[x_off_b + j],
+// times out_scale[r] when out_scale is not NULL.
+cudaError_t launch_gemv(int dtype, const void* M, const BlockDev* blocks, int b0, int nb,
+                        int na, const float* x, const float* out_scale, float* out,
+                        long long out_stride, cudaStream_t st);
+
+// Finalise: y = sum_b partial[b][r] (b ascending), times scale; w = y + q;
+// a = (1 - leak) a + gain w; optional clip; writes a and cmd.
+cudaError_t launch_finalise(const float* partial, int nblk, int na, const float* scale,
+                            const float* q, float* a, float* cmd, float one_minus_leak,
+                            float gain, int clip, float amin, float amax, cudaStream_t st);
+
+// Telemetry: compact copy of the padded slope buffer, block by block.
+cudaError_t launch_pack_slopes(const BlockDev* blocks, int nblk, int max_cols,
+                               const float* s_pad, float* out, cudaStream_t st);
+
+// Create-time relayout of a row-major [na][ns] matrix into column blocks (zero padding).
+cudaError_t launch_relayout(int dtype, const void* src, int na, int ns, const BlockDev* blocks,
+                            int nblk, int max_pitch, void* dst, cudaStream_t st);
+
+// Per-row scaled quantisation (rtc_quantize_rows).
+cudaError_t launch_quantize(int dtype, int na, int ns, const float* M, size_t ld, void* codes,
+                            float* scale, cudaStream_t st);
+
+// Finite check of a device float array; sets *bad (device int) to 1 if a NaN/Inf is found.
+cudaError_t launch_check_finite(const float* x, size_t n, int* bad, cudaStream_t st);
+
+}  // namespace rtc

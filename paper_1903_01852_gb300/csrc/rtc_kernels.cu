@@ -1,0 +1,426 @@
+// CUDA kernels of the AO real-time-control hot path (sm_103a).
+//
+//   slopes_kernel    calibration fused with SH centre of gravity / pyramid quad
+//                    difference, one CTA per slope row (Section 2.2, Fig. wfs_slopes)
+//   gemv_kernel      reconstruction MVM, one partial per column block, warp per
+//                    matrix row, 128-bit streaming loads (Section 2.3: the MVM
+//                    is memory-bandwidth bound); also the POLC product P a
+//   finalise_kernel  partial sums + POLC term + leaky integrator (Section 3, 3.4)
+//   pack / relayout / quantize / check kernels used at creation and for telemetry
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include "rtc_internal.h"
+
+namespace rtc {
+
+size_t dtype_size(int dtype) { return dtype == RTC_F32 ? 4 : dtype == RTC_BF16 ? 2 : 1; }
+int elems_per_16B(int dtype) { return int(16 / dtype_size(dtype)); }
+
+// ---------------------------------------------------------------------------
+// Calibration: c = (raw - dark) * flat in float32 (both operations rounded to
+// nearest, never contracted), then the threshold.  A pixel is lit iff c > T.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float calibrate(unsigned raw, float dark, float flat, float T, int mode) {
+    const float c = __fmul_rn(__fsub_rn(static_cast<float>(raw), dark), flat);
+    if (!(c > T)) return 0.0f;
+    return mode == RTC_THRESH_SUBTRACT ? __fsub_rn(c, T) : c;
+}
+
+// SH slope row: the CTA first reduces each pixel column of the subaperture
+// strip over its npx rows (column flux F_c and first moment in y), split in
+// `groups` row groups so narrow strips still use the whole CTA; then one
+// thread per valid subaperture adds its npx columns.
+__device__ void sh_row(const SlopeRow& row, const WfsDev& W, const uint16_t* __restrict__ px,
+                       long long pitch, const uint16_t* __restrict__ xlist,
+                       const float* __restrict__ ref, float* __restrict__ s_pad, float* sm) {
+    const int n = W.npx;
+    const int ws = W.nsubx * n;                 // strip width in pixels
+    const int x0 = W.ox;
+    const int y0 = W.oy + row.row * n;
+    const int q0 = x0 >> 2;                     // quads of 4 pixels aligned to absolute columns
+    const int nq = ((x0 + ws + 3) >> 2) - q0;
+    const int G = W.sh_groups;
+    float* colF = sm;                           // [G][ws]
+    float* colY = sm + G * ws;                  // [G][ws]
+    const float half = 0.5f * float(n - 1);
+
+    for (int idx = threadIdx.x; idx < nq * G; idx += blockDim.x) {
+        const int q = idx % nq;
+        const int g = idx / nq;
+        const int xa = (q0 + q) << 2;
+        float F[4] = {0.f, 0.f, 0.f, 0.f};
+        float Y[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
+        for (int r = g; r < n; r += G) {
+            const int yy = y0 + r;
+            const uint2 rw = __ldg(reinterpret_cast<const uint2*>(px + yy * pitch + xa));
+            const float4 d = __ldg(reinterpret_cast<const float4*>(W.dark + (size_t)yy * W.calib_pitch + xa));
+            const float4 f = __ldg(reinterpret_cast<const float4*>(W.flat + (size_t)yy * W.calib_pitch + xa));
+            const float yc = float(r) - half;
+            const float t0 = calibrate(rw.x & 0xffffu, d.x, f.x, W.threshold, W.thresh_mode);
+            const float t1 = calibrate(rw.x >> 16, d.y, f.y, W.threshold, W.thresh_mode);
+            const float t2 = calibrate(rw.y & 0xffffu, d.z, f.z, W.threshold, W.thresh_mode);
+            const float t3 = calibrate(rw.y >> 16, d.w, f.w, W.threshold, W.thresh_mode);
+            F[0] += t0; F[1] += t1; F[2] += t2; F[3] += t3;
+            Y[0] = fmaf(t0, yc, Y[0]); Y[1] = fmaf(t1, yc, Y[1]);
+            Y[2] = fmaf(t2, yc, Y[2]); Y[3] = fmaf(t3, yc, Y[3]);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int c = xa + k - x0;
+            if (c >= 0 && c < ws) { colF[g * ws + c] = F[k]; colY[g * ws + c] = Y[k]; }
+        }
+    }
+    __syncthreads();
+    for (int u = threadIdx.x; u < row.nunits; u += blockDim.x) {
+        const int cx = xlist[row.unit0 + u] * n;
+        float Fs = 0.f, Xs = 0.f, Ys = 0.f;
+        for (int k = 0; k < n; ++k) {
+            float fc = 0.f, yc = 0.f;
+            for (int g = 0; g < G; ++g) { fc += colF[g * ws + cx + k]; yc += colY[g * ws + cx + k]; }
+            Fs += fc;
+            Xs = fmaf(float(k) - half, fc, Xs);
+            Ys += yc;
+        }
+        float sx = 0.f, sy = 0.f;
+        if (Fs > 0.f) { sx = Xs / Fs; sy = Ys / Fs; }
+        if (ref) { sx -= ref[row.s_compact + 2 * u]; sy -= ref[row.s_compact + 2 * u + 1]; }
+        s_pad[row.s_pad + 2 * u] = sx;
+        s_pad[row.s_pad + 2 * u + 1] = sy;
+    }
+}
+
+// Pyramid slope row: one thread per valid pupil pixel reads the matching pixel
+// of the four pupil images A (top-left), B (top-right), C (bottom-left),
+// D (bottom-right); sx = (A+C-B-D)/N, sy = (A+B-C-D)/N with N = A+B+C+D.
+__device__ void pyr_row(const SlopeRow& row, const WfsDev& W, const uint16_t* __restrict__ px,
+                        long long pitch, const uint16_t* __restrict__ xlist,
+                        const float* __restrict__ ref, float* __restrict__ s_pad) {
+    const int i = row.row;
+    for (int u = threadIdx.x; u < row.nunits; u += blockDim.x) {
+        const int j = xlist[row.unit0 + u];
+        float v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int yy = W.qy[k] + i, xx = W.qx[k] + j;
+            const size_t m = (size_t)yy * W.calib_pitch + xx;
+            v[k] = calibrate(px[yy * pitch + xx], __ldg(W.dark + m), __ldg(W.flat + m), W.threshold,
+                             W.thresh_mode);
+        }
+        const float N = (v[0] + v[1]) + (v[2] + v[3]);
+        float sx = 0.f, sy = 0.f;
+        if (N > 0.f) {
+            sx = ((v[0] + v[2]) - (v[1] + v[3])) / N;
+            sy = ((v[0] + v[1]) - (v[2] + v[3])) / N;
+        }
+        if (ref) { sx -= ref[row.s_compact + 2 * u]; sy -= ref[row.s_compact + 2 * u + 1]; }
+        s_pad[row.s_pad + 2 * u] = sx;
+        s_pad[row.s_pad + 2 * u + 1] = sy;
+    }
+}
+
+struct SlopeArgs {
+    const SlopeRow* rows;
+    int row0;
+    const WfsDev* wfs;
+    FramePtrs fp;
+    const uint16_t* xlist;
+    const float* ref;
+    float* s_pad;
+};
+
+__global__ void __launch_bounds__(kSlopeThreads) slopes_kernel(const __grid_constant__ SlopeArgs a) {
+    extern __shared__ float sm[];
+    const SlopeRow row = a.rows[a.row0 + blockIdx.x];
+    const WfsDev W = a.wfs[row.wfs];
+    if (W.kind == RTC_WFS_SH)
+        sh_row(row, W, a.fp.px[row.wfs], a.fp.pitch[row.wfs], a.xlist, a.ref, a.s_pad, sm);
+    else
+        pyr_row(row, W, a.fp.px[row.wfs], a.fp.pitch[row.wfs], a.xlist, a.ref, a.s_pad);
+}
+
+cudaError_t configure_slopes(int smem_bytes) {
+    if (smem_bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(slopes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+}
+
+cudaError_t launch_slopes(const SlopeRow* rows, int row0, int nrows, const WfsDev* wfs,
+                          const FramePtrs& fp, const uint16_t* xlist, const float* ref,
+                          float* s_pad, int smem_bytes, cudaStream_t st) {
+    if (nrows <= 0) return cudaSuccess;
+    SlopeArgs a{rows, row0, wfs, fp, xlist, ref, s_pad};
+    slopes_kernel<<<nrows, kSlopeThreads, smem_bytes, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// GEMV: one warp per matrix row of a column block.  Each lane streams 16-byte
+// vectors v = lane, lane+32, ... of the row (U of them in flight), multiplies
+// by the matching input elements (read-only cache) and accumulates in float32;
+// a fixed xor-butterfly reduces the 32 lane sums.  The order of every sum is
+// fixed, so a block's partial does not depend on how the launch was split.
+// ---------------------------------------------------------------------------
+template <int DT> struct Elem;
+template <> struct Elem<RTC_F32> { static constexpr int kPer16 = 4; };
+template <> struct Elem<RTC_BF16> { static constexpr int kPer16 = 8; };
+template <> struct Elem<RTC_E4M3> { static constexpr int kPer16 = 16; };
+
+__device__ __forceinline__ uint4 ld_stream(const uint4* p) {
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ float bf_lo(uint32_t u) { return __uint_as_float(u << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
+
+__device__ __forceinline__ float dot_f32(const uint4& m, const float4* x, float acc) {
+    const float4 xv = __ldg(x);
+    acc = fmaf(__uint_as_float(m.x), xv.x, acc);
+    acc = fmaf(__uint_as_float(m.y), xv.y, acc);
+    acc = fmaf(__uint_as_float(m.z), xv.z, acc);
+    acc = fmaf(__uint_as_float(m.w), xv.w, acc);
+    return acc;
+}
+
+__device__ __forceinline__ float dot_bf16(const uint4& m, const float4* x, float acc) {
+    const float4 a = __ldg(x), b = __ldg(x + 1);
+    acc = fmaf(bf_lo(m.x), a.x, acc);
+    acc = fmaf(bf_hi(m.x), a.y, acc);
+    acc = fmaf(bf_lo(m.y), a.z, acc);
+    acc = fmaf(bf_hi(m.y), a.w, acc);
+    acc = fmaf(bf_lo(m.z), b.x, acc);
+    acc = fmaf(bf_hi(m.z), b.y, acc);
+    acc = fmaf(bf_lo(m.w), b.z, acc);
+    acc = fmaf(bf_hi(m.w), b.w, acc);
+    return acc;
+}
+
+__device__ __forceinline__ float2 e4m3x2(uint32_t pair16) {
+    const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>(pair16), __NV_E4M3);
+    return __half22float2(*reinterpret_cast<const __half2*>(&h));
+}
+
+__device__ __forceinline__ float dot_e4m3(const uint4& m, const float4* x, float acc) {
+    const uint32_t w[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float4 xv = __ldg(x + k);
+        const float2 lo = e4m3x2(w[k] & 0xffffu);
+        const float2 hi = e4m3x2(w[k] >> 16);
+        acc = fmaf(lo.x, xv.x, acc);
+        acc = fmaf(lo.y, xv.y, acc);
+        acc = fmaf(hi.x, xv.z, acc);
+        acc = fmaf(hi.y, xv.w, acc);
+    }
+    return acc;
+}
+
+template <int DT>
+__device__ __forceinline__ float dot16(const uint4& m, const float* x, int v, float acc) {
+    const float4* xp = reinterpret_cast<const float4*>(x) + v * (Elem<DT>::kPer16 / 4);
+    if constexpr (DT == RTC_F32) return dot_f32(m, xp, acc);
+    else if constexpr (DT == RTC_BF16) return dot_bf16(m, xp, acc);
+    else return dot_e4m3(m, xp, acc);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+struct GemvArgs {
+    const uint8_t* M;
+    const BlockDev* blocks;
+    int b0;
+    int tiles;                 // row tiles per block
+    int na;
+    const float* x;
+    const float* out_scale;
+    float* out;
+    long long out_stride;
+};
+
+template <int DT, int U, int RPW>
+__global__ void __launch_bounds__(kGemvWarps * 32) gemv_kernel(const __grid_constant__ GemvArgs a) {
+    const int bi = blockIdx.x / a.tiles;
+    const int tile = blockIdx.x - bi * a.tiles;
+    const int b = a.b0 + bi;
+    const BlockDev B = a.blocks[b];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nvec = B.pitch / Elem<DT>::kPer16;
+    const float* x = a.x + B.x_off;
+    const size_t esz = 16 / Elem<DT>::kPer16;
+    const int rbase = (tile * kGemvWarps + warp) * RPW;
+#pragma unroll 1
+    for (int rr = 0; rr < RPW; ++rr) {
+        const int r = rbase + rr;
+        if (r >= a.na) break;
+        const uint4* mrow = reinterpret_cast<const uint4*>(a.M + (size_t)(B.m_off + (long long)r * B.pitch) * esz);
+        float acc = 0.f;
+#pragma unroll 1
+        for (int v0 = lane; v0 < nvec; v0 += 32 * U) {
+            uint4 m[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int v = v0 + 32 * u;
+                m[u] = v < nvec ? ld_stream(mrow + v) : make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int v = v0 + 32 * u;
+                if (v < nvec) acc = dot16<DT>(m[u], x, v, acc);
+            }
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            if (a.out_scale) acc *= a.out_scale[r];
+            a.out[(long long)b * a.out_stride + r] = acc;
+        }
+    }
+}
+
+cudaError_t launch_gemv(int dtype, const void* M, const BlockDev* blocks, int b0, int nb, int na,
+                        const float* x, const float* out_scale, float* out, long long out_stride,
+                        cudaStream_t st) {
+    if (nb <= 0 || na <= 0) return cudaSuccess;
+    constexpr int U = 4, RPW = 4;
+    const int rows_per_cta = kGemvWarps * RPW;
+    const int tiles = (na + rows_per_cta - 1) / rows_per_cta;
+    GemvArgs a{static_cast<const uint8_t*>(M), blocks, b0, tiles, na, x, out_scale, out, out_stride};
+    const dim3 grid(tiles * nb);
+    switch (dtype) {
+        case RTC_F32: gemv_kernel<RTC_F32, U, RPW><<<grid, kGemvWarps * 32, 0, st>>>(a); break;
+        case RTC_BF16: gemv_kernel<RTC_BF16, U, RPW><<<grid, kGemvWarps * 32, 0, st>>>(a); break;
+        case RTC_E4M3: gemv_kernel<RTC_E4M3, U, RPW><<<grid, kGemvWarps * 32, 0, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Finalise: the master's sum of partial commands (Section 3) in block order,
+// the row scale of a quantised matrix, the implicit-POLC term q = P a_{k-1}
+// (Section 3.4) and the leaky integrator.  Commands go to device state and to
+// the page-locked ring (mapped host memory).
+// ---------------------------------------------------------------------------
+__global__ void finalise_kernel(const float* __restrict__ partial, int nblk, int na,
+                                const float* __restrict__ scale, const float* __restrict__ q,
+                                float* __restrict__ a, float* __restrict__ cmd, float oml, float gain,
+                                int clip, float amin, float amax) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= na) return;
+    float y = 0.f;
+    for (int b = 0; b < nblk; ++b) y += partial[(size_t)b * na + r];
+    if (scale) y *= scale[r];
+    const float w = y + q[r];
+    float v = fmaf(gain, w, oml * a[r]);
+    if (clip) v = fminf(fmaxf(v, amin), amax);
+    a[r] = v;
+    cmd[r] = v;
+}
+
+cudaError_t launch_finalise(const float* partial, int nblk, int na, const float* scale, const float* q,
+                            float* a, float* cmd, float oml, float gain, int clip, float amin, float amax,
+                            cudaStream_t st) {
+    finalise_kernel<<<(na + 255) / 256, 256, 0, st>>>(partial, nblk, na, scale, q, a, cmd, oml, gain, clip,
+                                                       amin, amax);
+    return cudaGetLastError();
+}
+
+__global__ void pack_slopes_kernel(const BlockDev* __restrict__ blocks, const float* __restrict__ s_pad,
+                                   float* __restrict__ out) {
+    const BlockDev B = blocks[blockIdx.y];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < B.ncols; j += gridDim.x * blockDim.x)
+        out[B.c0 + j] = s_pad[B.x_off + j];
+}
+
+cudaError_t launch_pack_slopes(const BlockDev* blocks, int nblk, int max_cols, const float* s_pad, float* out,
+                               cudaStream_t st) {
+    const dim3 grid((max_cols + 255) / 256, nblk);
+    pack_slopes_kernel<<<grid, 256, 0, st>>>(blocks, s_pad, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Creation-time helpers
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void relayout_kernel(const T* __restrict__ src, int na, int ns, const BlockDev* __restrict__ blocks,
+                                T* __restrict__ dst) {
+    const BlockDev B = blocks[blockIdx.y];
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)na * B.pitch;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = int(e / B.pitch), j = int(e - (long long)r * B.pitch);
+        dst[B.m_off + e] = j < B.ncols ? src[(size_t)r * ns + B.c0 + j] : T(0);
+    }
+}
+
+cudaError_t launch_relayout(int dtype, const void* src, int na, int ns, const BlockDev* blocks, int nblk,
+                            int max_pitch, void* dst, cudaStream_t st) {
+    const long long per = (long long)na * max_pitch;
+    const dim3 grid((unsigned)((per + 255) / 256 < 4096 ? (per + 255) / 256 : 4096), nblk);
+    switch (dtype_size(dtype)) {
+        case 4: relayout_kernel<uint32_t><<<grid, 256, 0, st>>>((const uint32_t*)src, na, ns, blocks, (uint32_t*)dst); break;
+        case 2: relayout_kernel<uint16_t><<<grid, 256, 0, st>>>((const uint16_t*)src, na, ns, blocks, (uint16_t*)dst); break;
+        default: relayout_kernel<uint8_t><<<grid, 256, 0, st>>>((const uint8_t*)src, na, ns, blocks, (uint8_t*)dst); break;
+    }
+    return cudaGetLastError();
+}
+
+// One CTA per row: max |M_rj| (exact, order-free), the scale, then the codes.
+__global__ void quantize_kernel(int dtype, int ns, const float* __restrict__ M, size_t ld, void* __restrict__ codes,
+                                float* __restrict__ scale) {
+    __shared__ float red[32];
+    const int r = blockIdx.x;
+    const float* row = M + (size_t)r * ld;
+    float m = 0.f;
+    for (int j = threadIdx.x; j < ns; j += blockDim.x) m = fmaxf(m, fabsf(row[j]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) red[0] = m;
+    }
+    __syncthreads();
+    float s = dtype == RTC_E4M3 ? __fdiv_rn(red[0], 448.0f) : red[0];
+    if (!(s > 0.f)) s = 1.0f;
+    if (threadIdx.x == 0) scale[r] = s;
+    if (dtype == RTC_BF16) {
+        __nv_bfloat16* out = static_cast<__nv_bfloat16*>(codes) + (size_t)r * ns;
+        for (int j = threadIdx.x; j < ns; j += blockDim.x) out[j] = __float2bfloat16_rn(__fdiv_rn(row[j], s));
+    } else {
+        __nv_fp8_storage_t* out = static_cast<__nv_fp8_storage_t*>(codes) + (size_t)r * ns;
+        for (int j = threadIdx.x; j < ns; j += blockDim.x)
+            out[j] = __nv_cvt_float_to_fp8(__fdiv_rn(row[j], s), __NV_SATFINITE, __NV_E4M3);
+    }
+}
+
+cudaError_t launch_quantize(int dtype, int na, int ns, const float* M, size_t ld, void* codes, float* scale,
+                            cudaStream_t st) {
+    if (na <= 0) return cudaSuccess;
+    quantize_kernel<<<na, 256, 0, st>>>(dtype, ns, M, ld, codes, scale);
+    return cudaGetLastError();
+}
+
+__global__ void check_finite_kernel(const float* __restrict__ x, size_t n, int* bad) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        if (!isfinite(x[i])) *bad = 1;
+}
+
+cudaError_t launch_check_finite(const float* x, size_t n, int* bad, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    size_t g = (n + 255) / 256;
+    if (g > 4096) g = 4096;
+    check_finite_kernel<<<(unsigned)g, 256, 0, st>>>(x, n, bad);
+    return cudaGetLastError();
+}
+
+}  // namespace rtc

@@ -1,0 +1,881 @@
+// Host runtime of the AO RTC library: loop objects, plans, streams, events,
+// the page-locked command ring and the C ABI declared in include/rtc.h.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "rtc_internal.h"
+
+using namespace rtc;
+
+namespace {
+
+thread_local std::string g_err;
+
+using Clock = std::chrono::steady_clock;
+
+size_t round_up(size_t x, size_t m) { return (x + m - 1) / m * m; }
+
+struct Slot {
+    uint64_t frame_id = 0;
+    bool used = false;        // holds a frame whose submission completed
+    bool chunked = false;
+    cudaEvent_t ev_start = nullptr, ev_tail = nullptr, ev_slopes = nullptr, ev_mvm = nullptr;
+    cudaEvent_t ev_final = nullptr, ev_polc = nullptr, ev_tel = nullptr;
+};
+
+}  // namespace
+
+struct rtc_loop {
+    int dev = 0;
+    uint32_t flags = 0;
+    int na = 0, ns = 0, nwfs = 0, nrows = 0, nblk = 0, ring = 0;
+    int m_dtype = RTC_F32, p_dtype = RTC_F32;
+    float gain = 0.f, leak = 0.f, amin = 0.f, amax = 0.f;
+    int clip = 0;
+    bool has_polc = false, timing = false, telemetry = false;
+
+    // host plans
+    std::vector<rtc_wfs> wfs;
+    std::vector<int> wfs_row0, wfs_nrows, wfs_blk0, wfs_nblk;
+    std::vector<int> row_ready;     // per table row: pixel rows of its WFS needed
+    std::vector<int> blk_row_end;   // per block: end (exclusive) of its slope rows within the WFS
+    std::vector<BlockDev> blocks_h;
+    int max_cols = 0, smem_bytes = 0;
+    uint64_t m_bytes = 0, p_bytes = 0, pixel_bytes = 0, device_bytes = 0;
+
+    // device buffers
+    void* d_M = nullptr;
+    float* d_Mscale = nullptr;
+    void* d_P = nullptr;
+    float* d_Pscale = nullptr;
+    BlockDev* d_blocks = nullptr;
+    BlockDev* d_pblock = nullptr;
+    std::vector<float*> d_dark, d_flat;
+    WfsDev* d_wfs = nullptr;
+    SlopeRow* d_rows = nullptr;
+    uint16_t* d_xlist = nullptr;
+    float* d_ref = nullptr;
+    std::vector<uint16_t*> d_frame;
+    std::vector<long long> frame_pitch;     // uint16 elements
+    float* d_s = nullptr;
+    float* d_part = nullptr;
+    float* d_a = nullptr;
+    float* d_q = nullptr;
+    std::vector<void*> allocs;              // everything cudaMalloc'd, for destroy
+
+    // page-locked ring: per slot na commands then ns slopes
+    float* h_ring = nullptr;
+    float* d_ring = nullptr;
+    size_t slot_floats = 0;
+    std::vector<Slot> slots;
+
+    cudaStream_t st = nullptr, st_tel = nullptr;
+
+    // frame state (submitting thread)
+    bool active = false;
+    uint64_t cur_id = 0;
+    bool have_last = false;
+    uint64_t last_id = 0;
+    int cur_slot = 0;
+    uint64_t seq = 0;
+    std::vector<int> rows_in, rows_done, blks_done;
+    bool tail_recorded = false;
+
+    // completed-submission queue (shared with readers)
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<int> pending;
+    uint64_t frames_done = 0, frames_dropped = 0, frames_overrun = 0;
+
+    std::string err;
+    bool broken = false;
+    bool cuda_touched = false;   // false until creation first calls into CUDA
+};
+
+namespace {
+
+int fail(rtc_loop* L, int code, const std::string& msg) {
+    if (L) L->err = msg;
+    else g_err = msg;
+    return code;
+}
+
+int cuda_fail(rtc_loop* L, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    if (L) L->broken = true;
+    return fail(L, RTC_ECUDA, m);
+}
+
+#define CK(L, call)                                                    \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) return cuda_fail((L), e_, #call);       \
+    } while (0)
+
+int use_device(rtc_loop* L) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != L->dev) CK(L, cudaSetDevice(L->dev));
+    return RTC_OK;
+}
+
+bool all_finite(const float* p, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+template <typename T>
+int dev_alloc(rtc_loop* L, T** p, size_t bytes) {
+    void* v = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&v, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(L, RTC_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    L->allocs.push_back(v);
+    L->device_bytes += bytes;
+    *p = static_cast<T*>(v);
+    return RTC_OK;
+}
+
+#define TRY(expr)                  \
+    do {                           \
+        int r_ = (expr);           \
+        if (r_ != RTC_OK) return r_; \
+    } while (0)
+
+void release(rtc_loop* L) {
+    if (!L) return;
+    if (!L->cuda_touched) {
+        delete L;
+        return;
+    }
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != L->dev) cudaSetDevice(L->dev);
+    if (L->st) cudaStreamSynchronize(L->st);
+    if (L->st_tel) cudaStreamSynchronize(L->st_tel);
+    for (auto& s : L->slots)
+        for (cudaEvent_t e : {s.ev_start, s.ev_tail, s.ev_slopes, s.ev_mvm, s.ev_final, s.ev_polc, s.ev_tel})
+            if (e) cudaEventDestroy(e);
+    for (void* p : L->allocs) cudaFree(p);
+    if (L->h_ring) cudaFreeHost(L->h_ring);
+    if (L->st) cudaStreamDestroy(L->st);
+    if (L->st_tel) cudaStreamDestroy(L->st_tel);
+    cudaGetLastError();
+    delete L;
+}
+
+int check_wfs(const rtc_wfs& w, int k) {
+    auto bad = [&](const char* what) {
+        return fail(nullptr, RTC_EINVAL, "wfs " + std::to_string(k) + ": " + what);
+    };
+    if (w.width <= 0 || w.height <= 0 || w.width > 65536 || w.height > 65536) return bad("bad frame size");
+    if (w.kind == RTC_WFS_SH) {
+        if (w.npx <= 0 || w.nsubx <= 0 || w.nsuby <= 0 || w.ox < 0 || w.oy < 0) return bad("bad SH grid");
+        if ((long long)w.ox + (long long)w.nsubx * w.npx > w.width ||
+            (long long)w.oy + (long long)w.nsuby * w.npx > w.height)
+            return bad("SH grid outside the frame");
+        if (w.nsubx > 65535) return bad("too many subapertures across");
+        if (w.nblocks < 1 || w.nblocks > w.nsuby) return bad("nblocks must be in [1, nsuby]");
+    } else if (w.kind == RTC_WFS_PYRAMID) {
+        if (w.pupil <= 0) return bad("bad pupil size");
+        for (int q = 0; q < 4; ++q)
+            if (w.qx[q] < 0 || w.qy[q] < 0 || w.qx[q] + w.pupil > w.width || w.qy[q] + w.pupil > w.height)
+                return bad("pupil image outside the frame");
+        if (w.nblocks < 1 || w.nblocks > w.pupil) return bad("nblocks must be in [1, pupil]");
+    } else {
+        return bad("unknown kind");
+    }
+    return RTC_OK;
+}
+
+// Upload a row-major [rows][cols] host matrix of `dtype` into column blocks.
+int upload_matrix(rtc_loop* L, int dtype, const void* host, int rows, int cols, const BlockDev* d_blocks,
+                  const std::vector<BlockDev>& blocks, void* dst, bool check_finite) {
+    const size_t esz = dtype_size(dtype);
+    const size_t bytes = (size_t)rows * cols * esz;
+    void* tmp = nullptr;
+    if (bytes) {
+        if (cudaMalloc(&tmp, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(L, RTC_ENOMEM, "temporary upload buffer of " + std::to_string(bytes) + " bytes");
+        }
+    }
+    int rc = RTC_OK;
+    int* d_bad = nullptr;
+    cudaError_t e = cudaSuccess;
+    int max_pitch = 0;
+    for (auto& b : blocks) max_pitch = std::max(max_pitch, b.pitch);
+    if (bytes) e = cudaMemcpy(tmp, host, bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && check_finite && dtype == RTC_F32 && bytes) {
+        e = cudaMalloc(&d_bad, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(d_bad, 0, sizeof(int));
+        if (e == cudaSuccess) e = launch_check_finite(static_cast<const float*>(tmp), (size_t)rows * cols, d_bad, L->st);
+        int bad = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, L->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(L->st);
+        if (e == cudaSuccess && bad) rc = fail(L, RTC_EINVAL, "matrix contains NaN or Inf");
+    }
+    if (e == cudaSuccess && rc == RTC_OK && max_pitch > 0)
+        e = launch_relayout(dtype, tmp, rows, cols, d_blocks, (int)blocks.size(), max_pitch, dst, L->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(L->st);
+    if (d_bad) cudaFree(d_bad);
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(L, e, "matrix upload");
+    return rc;
+}
+
+int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, const rtc_polc* P, rtc_loop* L) {
+    if (!G || !M || !P) return fail(L, RTC_EINVAL, "geometry, cmat and polc are required");
+    if (G->nwfs < 1 || G->nwfs > kMaxWfs || !G->wfs) return fail(L, RTC_EINVAL, "nwfs must be in [1, 16]");
+    for (int k = 0; k < G->nwfs; ++k) TRY(check_wfs(G->wfs[k], k));
+    if (M->dtype < RTC_F32 || M->dtype > RTC_E4M3 || !M->data || M->na < 1)
+        return fail(L, RTC_EINVAL, "bad control matrix description");
+    if (P->P && (P->dtype < RTC_F32 || P->dtype > RTC_E4M3)) return fail(L, RTC_EINVAL, "bad POLC dtype");
+    if (!std::isfinite(P->gain) || !std::isfinite(P->leak)) return fail(L, RTC_EINVAL, "gain/leak not finite");
+    if (P->clip && !(P->amin <= P->amax)) return fail(L, RTC_EINVAL, "clip needs amin <= amax");
+
+    L->dev = G->device;
+    L->flags = G->flags;
+    L->timing = (G->flags & RTC_FLAG_TIMING) != 0;
+    L->telemetry = (G->flags & RTC_FLAG_TELEMETRY) != 0;
+    L->ring = G->ring > 0 ? G->ring : 4;
+    if (L->ring < 2 || L->ring > 1024) return fail(L, RTC_EINVAL, "ring must be in [2, 1024]");
+    L->nwfs = G->nwfs;
+    L->na = M->na;
+    L->m_dtype = M->dtype;
+    L->p_dtype = P->P ? P->dtype : RTC_F32;
+    L->has_polc = P->P != nullptr;
+    L->gain = P->gain;
+    L->leak = P->leak;
+    L->clip = P->clip;
+    L->amin = P->amin;
+    L->amax = P->amax;
+    L->cuda_touched = true;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || L->dev < 0 || L->dev >= ndev) {
+        cudaGetLastError();
+        return fail(L, RTC_EINVAL, "no such CUDA device");
+    }
+    CK(L, cudaSetDevice(L->dev));
+
+    // ---- slope-row and block plans ------------------------------------
+    const int V = elems_per_16B(L->m_dtype);
+    std::vector<SlopeRow> rows;
+    std::vector<uint16_t> xlist;
+    std::vector<WfsDev> wdev(L->nwfs);
+    int compact = 0;
+    long long m_off = 0;
+    int x_off = 0;
+    L->wfs.assign(G->wfs, G->wfs + G->nwfs);
+    for (int k = 0; k < L->nwfs; ++k) {
+        const rtc_wfs& w = L->wfs[k];
+        const bool sh = w.kind == RTC_WFS_SH;
+        const int nr = sh ? w.nsuby : w.pupil;
+        const int nc = sh ? w.nsubx : w.pupil;
+        std::vector<int> units(nr);
+        std::vector<std::vector<uint16_t>> row_x(nr);
+        for (int i = 0; i < nr; ++i)
+            for (int j = 0; j < nc; ++j)
+                if (!w.valid || w.valid[(size_t)i * nc + j]) row_x[i].push_back((uint16_t)j);
+        L->wfs_row0.push_back((int)rows.size());
+        L->wfs_nrows.push_back(nr);
+        L->wfs_blk0.push_back((int)L->blocks_h.size());
+        L->wfs_nblk.push_back(w.nblocks);
+        for (int b = 0; b < w.nblocks; ++b) {
+            const int r0 = (int)((long long)b * nr / w.nblocks), r1 = (int)((long long)(b + 1) * nr / w.nblocks);
+            BlockDev B{};
+            B.m_off = m_off;
+            B.x_off = x_off;
+            B.c0 = compact;
+            int local = 0;
+            for (int i = r0; i < r1; ++i) {
+                SlopeRow R{};
+                R.wfs = k;
+                R.row = i;
+                R.unit0 = (int)xlist.size();
+                R.nunits = (int)row_x[i].size();
+                R.s_pad = x_off + local;
+                R.s_compact = compact + local;
+                rows.push_back(R);
+                L->row_ready.push_back(sh ? w.oy + (i + 1) * w.npx
+                                          : *std::max_element(w.qy, w.qy + 4) + i + 1);
+                xlist.insert(xlist.end(), row_x[i].begin(), row_x[i].end());
+                local += 2 * R.nunits;
+            }
+            B.ncols = local;
+            B.pitch = (int)round_up((size_t)local, (size_t)V);
+            compact += local;
+            x_off += B.pitch;
+            m_off += (long long)L->na * B.pitch;
+            L->blk_row_end.push_back(r1);
+            L->blocks_h.push_back(B);
+            L->max_cols = std::max(L->max_cols, B.ncols);
+        }
+        WfsDev& D = wdev[k];
+        D.kind = w.kind;
+        D.width = w.width;
+        D.height = w.height;
+        D.npx = w.npx;
+        D.nsubx = w.nsubx;
+        D.nsuby = w.nsuby;
+        D.ox = w.ox;
+        D.oy = w.oy;
+        D.pupil = w.pupil;
+        for (int q = 0; q < 4; ++q) { D.qx[q] = w.qx[q]; D.qy[q] = w.qy[q]; }
+        D.threshold = (C && C->threshold) ? C->threshold[k] : 0.f;
+        D.thresh_mode = (C && C->thresh_mode) ? C->thresh_mode[k] : RTC_THRESH_SUBTRACT;
+        if (!(D.threshold >= 0.f) || !std::isfinite(D.threshold)) return fail(L, RTC_EINVAL, "threshold must be finite and >= 0");
+        if (D.thresh_mode != RTC_THRESH_SUBTRACT && D.thresh_mode != RTC_THRESH_CLIP)
+            return fail(L, RTC_EINVAL, "bad threshold mode");
+        D.calib_pitch = (int)round_up((size_t)w.width, 4);
+        if (sh) {
+            const int ws = w.nsubx * w.npx;
+            const int nq = ((w.ox + ws + 3) >> 2) - (w.ox >> 2);
+            D.sh_groups = std::max(1, std::min(w.npx, kSlopeThreads / nq));
+            L->smem_bytes = std::max(L->smem_bytes, (int)(2 * D.sh_groups * ws * sizeof(float)));
+            L->pixel_bytes += (size_t)w.nsuby * w.npx * (size_t)nq * 4 * (2 + 8);
+        }
+    }
+    // pyramid pixel bytes: 4 pixels x (2 + 8) bytes per valid unit
+    for (int k = 0; k < L->nwfs; ++k)
+        if (L->wfs[k].kind == RTC_WFS_PYRAMID) {
+            size_t n = 0;
+            for (int r = L->wfs_row0[k]; r < L->wfs_row0[k] + L->wfs_nrows[k]; ++r) n += rows[r].nunits;
+            L->pixel_bytes += n * 4 * (2 + 8);
+        }
+    L->nrows = (int)rows.size();
+    L->nblk = (int)L->blocks_h.size();
+    L->ns = compact;
+    if (M->ns != L->ns)
+        return fail(L, RTC_EINVAL, "cmat ns = " + std::to_string(M->ns) + " but the geometry has " +
+                                       std::to_string(L->ns) + " slopes");
+    if (L->smem_bytes > 200 * 1024) return fail(L, RTC_EINVAL, "subaperture strip too wide for shared memory");
+    if (L->smem_bytes < 16) L->smem_bytes = 16;
+    const int s_len = std::max(x_off, 4);
+    const int VP = elems_per_16B(L->p_dtype);
+    const int a_len = (int)round_up((size_t)L->na, 16);
+    L->m_bytes = (uint64_t)m_off * dtype_size(L->m_dtype);
+
+    // ---- host-side checks of the maps --------------------------------
+    if (C && C->ref_slopes && !all_finite(C->ref_slopes, L->ns)) return fail(L, RTC_EINVAL, "ref_slopes not finite");
+    if (M->row_scale && !all_finite(M->row_scale, L->na)) return fail(L, RTC_EINVAL, "row_scale not finite");
+    if (P->P && P->row_scale && !all_finite(P->row_scale, L->na)) return fail(L, RTC_EINVAL, "P row_scale not finite");
+    if (P->a0 && !all_finite(P->a0, L->na)) return fail(L, RTC_EINVAL, "a0 not finite");
+    for (int k = 0; k < L->nwfs; ++k) {
+        const size_t n = (size_t)L->wfs[k].width * L->wfs[k].height;
+        if (C && C->dark && C->dark[k] && !all_finite(C->dark[k], n)) return fail(L, RTC_EINVAL, "dark map not finite");
+        if (C && C->flat && C->flat[k] && !all_finite(C->flat[k], n)) return fail(L, RTC_EINVAL, "flat map not finite");
+    }
+
+    // ---- HBM admission --------------------------------------------------
+    size_t need = L->m_bytes + (size_t)L->na * M->ns * dtype_size(L->m_dtype);  // stored + upload temporary
+    if (L->has_polc) need += (size_t)L->na * round_up(L->na, VP) * dtype_size(L->p_dtype) * 2;
+    for (auto& w : L->wfs) need += (size_t)w.height * (round_up(w.width, 4) * 8 + round_up(w.width, 8) * 2);
+    need += (size_t)L->nblk * L->na * 4 + (size_t)s_len * 4 + (size_t)a_len * 8;
+    size_t free_b = 0, total_b = 0;
+    CK(L, cudaMemGetInfo(&free_b, &total_b));
+    if (need + (64u << 20) > free_b)
+        return fail(L, RTC_ENOMEM, "loop needs " + std::to_string(need) + " bytes of device memory, " +
+                                       std::to_string(free_b) + " free");
+
+    CK(L, configure_slopes(L->smem_bytes));
+    CK(L, cudaStreamCreateWithPriority(&L->st, cudaStreamNonBlocking, -5));   // clamped to the highest priority
+    CK(L, cudaStreamCreateWithFlags(&L->st_tel, cudaStreamNonBlocking));
+
+    // ---- device buffers ---------------------------------------------------
+    TRY(dev_alloc(L, &L->d_blocks, L->blocks_h.size() * sizeof(BlockDev)));
+    CK(L, cudaMemcpy(L->d_blocks, L->blocks_h.data(), L->blocks_h.size() * sizeof(BlockDev), cudaMemcpyHostToDevice));
+    TRY(dev_alloc(L, &L->d_M, L->m_bytes));
+    TRY(upload_matrix(L, L->m_dtype, M->data, L->na, L->ns, L->d_blocks, L->blocks_h, L->d_M, true));
+    if (M->row_scale) {
+        TRY(dev_alloc(L, &L->d_Mscale, (size_t)L->na * 4));
+        CK(L, cudaMemcpy(L->d_Mscale, M->row_scale, (size_t)L->na * 4, cudaMemcpyHostToDevice));
+    }
+    if (L->has_polc) {
+        BlockDev PB{};
+        PB.m_off = 0;
+        PB.x_off = 0;
+        PB.ncols = L->na;
+        PB.pitch = (int)round_up((size_t)L->na, VP);
+        PB.c0 = 0;
+        L->p_bytes = (uint64_t)L->na * PB.pitch * dtype_size(L->p_dtype);
+        TRY(dev_alloc(L, &L->d_pblock, sizeof(BlockDev)));
+        CK(L, cudaMemcpy(L->d_pblock, &PB, sizeof(BlockDev), cudaMemcpyHostToDevice));
+        TRY(dev_alloc(L, &L->d_P, L->p_bytes));
+        TRY(upload_matrix(L, L->p_dtype, P->P, L->na, L->na, L->d_pblock, std::vector<BlockDev>{PB}, L->d_P, true));
+        if (P->row_scale) {
+            TRY(dev_alloc(L, &L->d_Pscale, (size_t)L->na * 4));
+            CK(L, cudaMemcpy(L->d_Pscale, P->row_scale, (size_t)L->na * 4, cudaMemcpyHostToDevice));
+        }
+    }
+    // calibration maps and frame buffers
+    L->d_dark.resize(L->nwfs);
+    L->d_flat.resize(L->nwfs);
+    L->d_frame.resize(L->nwfs);
+    L->frame_pitch.resize(L->nwfs);
+    for (int k = 0; k < L->nwfs; ++k) {
+        const rtc_wfs& w = L->wfs[k];
+        const size_t cp = round_up(w.width, 4);
+        TRY(dev_alloc(L, &L->d_dark[k], (size_t)w.height * cp * 4));
+        TRY(dev_alloc(L, &L->d_flat[k], (size_t)w.height * cp * 4));
+        CK(L, cudaMemset(L->d_dark[k], 0, (size_t)w.height * cp * 4));
+        const float* dk = (C && C->dark) ? C->dark[k] : nullptr;
+        const float* fl = (C && C->flat) ? C->flat[k] : nullptr;
+        if (dk) CK(L, cudaMemcpy2D(L->d_dark[k], cp * 4, dk, (size_t)w.width * 4, (size_t)w.width * 4, w.height,
+                                   cudaMemcpyHostToDevice));
+        std::vector<float> ones;
+        if (!fl) {
+            ones.assign((size_t)w.height * cp, 1.0f);
+            CK(L, cudaMemcpy(L->d_flat[k], ones.data(), ones.size() * 4, cudaMemcpyHostToDevice));
+        } else {
+            CK(L, cudaMemset(L->d_flat[k], 0, (size_t)w.height * cp * 4));
+            CK(L, cudaMemcpy2D(L->d_flat[k], cp * 4, fl, (size_t)w.width * 4, (size_t)w.width * 4, w.height,
+                               cudaMemcpyHostToDevice));
+        }
+        wdev[k].dark = L->d_dark[k];
+        wdev[k].flat = L->d_flat[k];
+        const size_t fp = round_up(w.width, 8);
+        L->frame_pitch[k] = (long long)fp;
+        TRY(dev_alloc(L, &L->d_frame[k], (size_t)w.height * fp * 2));
+        CK(L, cudaMemset(L->d_frame[k], 0, (size_t)w.height * fp * 2));
+    }
+    TRY(dev_alloc(L, &L->d_wfs, wdev.size() * sizeof(WfsDev)));
+    CK(L, cudaMemcpy(L->d_wfs, wdev.data(), wdev.size() * sizeof(WfsDev), cudaMemcpyHostToDevice));
+    TRY(dev_alloc(L, &L->d_rows, rows.size() * sizeof(SlopeRow)));
+    CK(L, cudaMemcpy(L->d_rows, rows.data(), rows.size() * sizeof(SlopeRow), cudaMemcpyHostToDevice));
+    TRY(dev_alloc(L, &L->d_xlist, std::max<size_t>(xlist.size(), 1) * 2));
+    if (!xlist.empty()) CK(L, cudaMemcpy(L->d_xlist, xlist.data(), xlist.size() * 2, cudaMemcpyHostToDevice));
+    if (C && C->ref_slopes) {
+        TRY(dev_alloc(L, &L->d_ref, (size_t)L->ns * 4));
+        CK(L, cudaMemcpy(L->d_ref, C->ref_slopes, (size_t)L->ns * 4, cudaMemcpyHostToDevice));
+    }
+    TRY(dev_alloc(L, &L->d_s, (size_t)s_len * 4));
+    CK(L, cudaMemset(L->d_s, 0, (size_t)s_len * 4));
+    TRY(dev_alloc(L, &L->d_part, (size_t)std::max(L->nblk, 1) * L->na * 4));
+    CK(L, cudaMemset(L->d_part, 0, (size_t)std::max(L->nblk, 1) * L->na * 4));
+    TRY(dev_alloc(L, &L->d_a, (size_t)std::max(a_len, (int)round_up(L->na, VP)) * 4));
+    CK(L, cudaMemset(L->d_a, 0, (size_t)std::max(a_len, (int)round_up(L->na, VP)) * 4));
+    if (P->a0) CK(L, cudaMemcpy(L->d_a, P->a0, (size_t)L->na * 4, cudaMemcpyHostToDevice));
+    TRY(dev_alloc(L, &L->d_q, (size_t)L->na * 4));
+    CK(L, cudaMemset(L->d_q, 0, (size_t)L->na * 4));
+    if (L->has_polc) {
+        CK(L, launch_gemv(L->p_dtype, L->d_P, L->d_pblock, 0, 1, L->na, L->d_a, L->d_Pscale, L->d_q, 0, L->st));
+    }
+
+    // ---- page-locked ring, events -------------------------------------------
+    L->slot_floats = round_up((size_t)L->na, 4) + round_up((size_t)L->ns, 4);
+    {
+        void* h = nullptr;
+        cudaError_t e = cudaHostAlloc(&h, (size_t)L->ring * L->slot_floats * 4, cudaHostAllocMapped);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(L, RTC_ENOMEM, "page-locked command ring");
+        }
+        L->h_ring = static_cast<float*>(h);
+        std::memset(L->h_ring, 0, (size_t)L->ring * L->slot_floats * 4);
+        void* d = nullptr;
+        CK(L, cudaHostGetDevicePointer(&d, h, 0));
+        L->d_ring = static_cast<float*>(d);
+    }
+    L->slots.resize(L->ring);
+    const unsigned evflags = L->timing ? cudaEventDefault : cudaEventDisableTiming;
+    for (auto& s : L->slots) {
+        CK(L, cudaEventCreateWithFlags(&s.ev_final, evflags));
+        CK(L, cudaEventCreateWithFlags(&s.ev_tel, cudaEventDisableTiming));
+        if (L->timing) {
+            CK(L, cudaEventCreate(&s.ev_start));
+            CK(L, cudaEventCreate(&s.ev_tail));
+            CK(L, cudaEventCreate(&s.ev_slopes));
+            CK(L, cudaEventCreate(&s.ev_mvm));
+            CK(L, cudaEventCreate(&s.ev_polc));
+        }
+    }
+    L->rows_in.assign(L->nwfs, 0);
+    L->rows_done.assign(L->nwfs, 0);
+    L->blks_done.assign(L->nwfs, 0);
+    CK(L, cudaStreamSynchronize(L->st));
+    return RTC_OK;
+}
+
+// Start a frame: pick its ring slot (discarding an unread frame that still holds it).
+void begin_frame(rtc_loop* L, uint64_t id, bool chunked) {
+    L->active = chunked;
+    L->cur_id = id;
+    L->cur_slot = (int)(L->seq % (uint64_t)L->ring);
+    {
+        std::lock_guard<std::mutex> g(L->mu);
+        auto it = std::find(L->pending.begin(), L->pending.end(), L->cur_slot);
+        if (it != L->pending.end()) {
+            L->pending.erase(it);
+            ++L->frames_overrun;
+        }
+        Slot& s = L->slots[L->cur_slot];
+        s.used = false;
+        s.frame_id = id;
+        s.chunked = chunked;
+    }
+    std::fill(L->rows_in.begin(), L->rows_in.end(), 0);
+    std::fill(L->rows_done.begin(), L->rows_done.end(), 0);
+    std::fill(L->blks_done.begin(), L->blks_done.end(), 0);
+    L->tail_recorded = false;
+}
+
+// Finalise, POLC for the next frame, telemetry, then publish the slot.
+int finish_frame(rtc_loop* L) {
+    Slot& s = L->slots[L->cur_slot];
+    float* cmd = L->d_ring + (size_t)L->cur_slot * L->slot_floats;
+    CK(L, launch_finalise(L->d_part, L->nblk, L->na, L->d_Mscale, L->d_q, L->d_a, cmd, 1.0f - L->leak, L->gain,
+                          L->clip, L->amin, L->amax, L->st));
+    CK(L, cudaEventRecord(s.ev_final, L->st));
+    if (L->telemetry) {
+        CK(L, cudaStreamWaitEvent(L->st_tel, s.ev_final, 0));
+        CK(L, launch_pack_slopes(L->d_blocks, L->nblk, std::max(L->max_cols, 1), L->d_s,
+                                 cmd + round_up((size_t)L->na, 4), L->st_tel));
+        CK(L, cudaEventRecord(s.ev_tel, L->st_tel));
+    } else {
+        CK(L, cudaEventRecord(s.ev_tel, L->st));
+    }
+    if (L->has_polc)
+        CK(L, launch_gemv(L->p_dtype, L->d_P, L->d_pblock, 0, 1, L->na, L->d_a, L->d_Pscale, L->d_q, 0, L->st));
+    if (L->timing) CK(L, cudaEventRecord(s.ev_polc, L->st));
+    if (L->telemetry) CK(L, cudaStreamWaitEvent(L->st, s.ev_tel, 0));   // the next frame rewrites the slopes
+    {
+        std::lock_guard<std::mutex> g(L->mu);
+        s.used = true;
+        L->pending.push_back(L->cur_slot);
+        ++L->frames_done;
+    }
+    L->cv.notify_all();
+    L->active = false;
+    L->have_last = true;
+    L->last_id = L->cur_id;
+    ++L->seq;
+    return RTC_OK;
+}
+
+FramePtrs internal_frames(rtc_loop* L) {
+    FramePtrs fp{};
+    for (int k = 0; k < L->nwfs; ++k) {
+        fp.px[k] = L->d_frame[k];
+        fp.pitch[k] = L->frame_pitch[k];
+    }
+    return fp;
+}
+
+int submit_impl(rtc_loop* L, const rtc_chunk* c) {
+    if (!c || c->wfs < 0 || c->wfs >= L->nwfs || !c->px) return fail(L, RTC_EINVAL, "bad chunk");
+    const rtc_wfs& w = L->wfs[c->wfs];
+    if (c->row_begin < 0 || c->row_end > w.height || c->row_begin >= c->row_end)
+        return fail(L, RTC_EINVAL, "bad chunk rows");
+    if (c->pitch < (size_t)w.width * 2) return fail(L, RTC_EINVAL, "chunk pitch smaller than a row");
+    int status = RTC_OK;
+    // order checks before any state change
+    if (L->active && c->frame_id != L->cur_id) {
+        if (c->frame_id < L->cur_id) return fail(L, RTC_EORDER, "chunk of an older frame");
+        if (c->row_begin != 0) return fail(L, RTC_EORDER, "new frame must start at row 0");
+        ++L->frames_dropped;
+        L->active = false;
+        status = RTC_EDROPPED;
+        L->err = "frame " + std::to_string(L->cur_id) + " was incomplete and has been dropped";
+    }
+    if (!L->active) {
+        if (L->have_last && c->frame_id <= L->last_id) return fail(L, RTC_EORDER, "frame id not increasing");
+        if (c->row_begin != 0) return fail(L, RTC_EORDER, "a frame must start at row 0");
+        begin_frame(L, c->frame_id, true);
+        if (L->timing) CK(L, cudaEventRecord(L->slots[L->cur_slot].ev_start, L->st));
+    } else if (c->row_begin != L->rows_in[c->wfs]) {
+        return fail(L, RTC_EORDER, "rows of a WFS must arrive in order without gaps");
+    }
+    const int k = c->wfs;
+    Slot& s = L->slots[L->cur_slot];
+    // last chunk of the frame?
+    bool last = true;
+    for (int j = 0; j < L->nwfs; ++j) {
+        const int got = j == k ? c->row_end : L->rows_in[j];
+        if (got < L->wfs[j].height) last = false;
+    }
+    if (last && L->timing) CK(L, cudaEventRecord(s.ev_tail, L->st));
+    CK(L, cudaMemcpy2DAsync(L->d_frame[k] + (size_t)c->row_begin * L->frame_pitch[k], L->frame_pitch[k] * 2, c->px,
+                            c->pitch, (size_t)w.width * 2, c->row_end - c->row_begin, cudaMemcpyDefault, L->st));
+    L->rows_in[k] = c->row_end;
+    // slope rows completed by these rows
+    const int r0 = L->wfs_row0[k];
+    int done = L->rows_done[k];
+    int upto = done;
+    while (upto < L->wfs_nrows[k] && L->row_ready[r0 + upto] <= L->rows_in[k]) ++upto;
+    if (upto > done) {
+        CK(L, launch_slopes(L->d_rows, r0 + done, upto - done, L->d_wfs, internal_frames(L), L->d_xlist, L->d_ref,
+                            L->d_s, L->smem_bytes, L->st));
+        L->rows_done[k] = upto;
+    }
+    if (last && L->timing) CK(L, cudaEventRecord(s.ev_slopes, L->st));
+    // column blocks completed by those slope rows
+    const int b0 = L->wfs_blk0[k];
+    int bd = L->blks_done[k];
+    int bu = bd;
+    while (bu < L->wfs_nblk[k] && L->blk_row_end[b0 + bu] <= L->rows_done[k]) ++bu;
+    if (bu > bd) {
+        CK(L, launch_gemv(L->m_dtype, L->d_M, L->d_blocks, b0 + bd, bu - bd, L->na, L->d_s, nullptr, L->d_part, L->na,
+                          L->st));
+        L->blks_done[k] = bu;
+    }
+    if (last) {
+        if (L->timing) CK(L, cudaEventRecord(s.ev_mvm, L->st));
+        TRY(finish_frame(L));
+    }
+    return status;
+}
+
+int process_impl(rtc_loop* L, uint64_t id, const uint16_t* const* px, const size_t* pitch) {
+    if (!px || !pitch) return fail(L, RTC_EINVAL, "px and pitch are required");
+    FramePtrs fp{};
+    for (int k = 0; k < L->nwfs; ++k) {
+        const rtc_wfs& w = L->wfs[k];
+        if (!px[k] || (reinterpret_cast<uintptr_t>(px[k]) & 15u) || (pitch[k] & 15u) ||
+            pitch[k] < round_up((size_t)w.width * 2, 16))
+            return fail(L, RTC_EINVAL, "frame " + std::to_string(k) + ": pointer/pitch not 16-byte aligned or too small");
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, px[k]) != cudaSuccess ||
+            (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+            cudaGetLastError();
+            return fail(L, RTC_EINVAL, "frame " + std::to_string(k) + " is not device memory");
+        }
+        fp.px[k] = px[k];
+        fp.pitch[k] = (long long)(pitch[k] / 2);
+    }
+    int status = RTC_OK;
+    if (L->active ? id <= L->cur_id : (L->have_last && id <= L->last_id))
+        return fail(L, RTC_EORDER, "frame id not increasing");
+    if (L->active) {
+        ++L->frames_dropped;
+        L->active = false;
+        status = RTC_EDROPPED;
+        L->err = "frame " + std::to_string(L->cur_id) + " was incomplete and has been dropped";
+    }
+    begin_frame(L, id, false);
+    Slot& s = L->slots[L->cur_slot];
+    if (L->timing) {
+        CK(L, cudaEventRecord(s.ev_start, L->st));
+        CK(L, cudaEventRecord(s.ev_tail, L->st));
+    }
+    CK(L, launch_slopes(L->d_rows, 0, L->nrows, L->d_wfs, fp, L->d_xlist, L->d_ref, L->d_s, L->smem_bytes, L->st));
+    if (L->timing) CK(L, cudaEventRecord(s.ev_slopes, L->st));
+    CK(L, launch_gemv(L->m_dtype, L->d_M, L->d_blocks, 0, L->nblk, L->na, L->d_s, nullptr, L->d_part, L->na, L->st));
+    if (L->timing) CK(L, cudaEventRecord(s.ev_mvm, L->st));
+    TRY(finish_frame(L));
+    return status;
+}
+
+// Busy-poll an event until done or the deadline.
+int wait_event(rtc_loop* L, cudaEvent_t ev, Clock::time_point deadline, bool forever) {
+    for (;;) {
+        cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return RTC_OK;
+        if (e != cudaErrorNotReady) return cuda_fail(L, e, "cudaEventQuery");
+        if (!forever && Clock::now() >= deadline) return fail(L, RTC_ETIMEDOUT, "timed out waiting for the GPU");
+    }
+}
+
+Clock::time_point deadline_of(int64_t us) {
+    return Clock::now() + std::chrono::microseconds(us < 0 ? 0 : us);
+}
+
+int find_slot(rtc_loop* L, uint64_t frame_id) {
+    std::lock_guard<std::mutex> g(L->mu);
+    for (int i = 0; i < L->ring; ++i)
+        if (L->slots[i].used && L->slots[i].frame_id == frame_id) return i;
+    return -1;
+}
+
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+        cudaGetLastError();
+        return -1.f;
+    }
+    return ms * 1000.f;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rtc_create(const rtc_geometry* geometry, const rtc_calib* calib, const rtc_cmat* cmat, const rtc_polc* polc,
+               rtc_loop** out) {
+    if (!out) return fail(nullptr, RTC_EINVAL, "out is NULL");
+    *out = nullptr;
+    rtc_loop* L = new (std::nothrow) rtc_loop();
+    if (!L) return fail(nullptr, RTC_ENOMEM, "host allocation failed");
+    int rc = create_impl(geometry, calib, cmat, polc, L);
+    if (rc != RTC_OK) {
+        g_err = L->err.empty() ? g_err : L->err;
+        release(L);
+        return rc;
+    }
+    *out = L;
+    return RTC_OK;
+}
+
+int rtc_destroy(rtc_loop* loop) {
+    release(loop);
+    return RTC_OK;
+}
+
+int rtc_submit_pixels(rtc_loop* L, const rtc_chunk* chunk) {
+    if (!L) return fail(nullptr, RTC_EINVAL, "loop is NULL");
+    if (L->broken) return fail(L, RTC_ECUDA, "loop is in a failed state: " + L->err);
+    TRY(use_device(L));
+    return submit_impl(L, chunk);
+}
+
+int rtc_process_frame(rtc_loop* L, uint64_t frame_id, const uint16_t* const* px, const size_t* pitch) {
+    if (!L) return fail(nullptr, RTC_EINVAL, "loop is NULL");
+    if (L->broken) return fail(L, RTC_ECUDA, "loop is in a failed state: " + L->err);
+    TRY(use_device(L));
+    return process_impl(L, frame_id, px, pitch);
+}
+
+int rtc_get_commands(rtc_loop* L, float* out, size_t n, uint64_t* frame_id, int64_t timeout_us) {
+    if (!L) return fail(nullptr, RTC_EINVAL, "loop is NULL");
+    if (!out || n != (size_t)L->na) return fail(L, RTC_EINVAL, "out must hold na floats");
+    TRY(use_device(L));
+    const bool forever = timeout_us < 0;
+    const auto deadline = deadline_of(timeout_us);
+    for (;;) {
+        int slot;
+        {
+            std::unique_lock<std::mutex> g(L->mu);
+            while (L->pending.empty()) {
+                if (forever) L->cv.wait(g);
+                else if (L->cv.wait_until(g, deadline) == std::cv_status::timeout && L->pending.empty())
+                    return fail(L, RTC_ETIMEDOUT, "no frame pending");
+            }
+            slot = L->pending.front();
+        }
+        TRY(wait_event(L, L->slots[slot].ev_final, deadline, forever));
+        std::lock_guard<std::mutex> g(L->mu);
+        if (L->pending.empty() || L->pending.front() != slot) continue;   // discarded meanwhile
+        L->pending.pop_front();
+        std::memcpy(out, L->h_ring + (size_t)slot * L->slot_floats, (size_t)L->na * 4);
+        if (frame_id) *frame_id = L->slots[slot].frame_id;
+        return RTC_OK;
+    }
+}
+
+int rtc_get_telemetry(rtc_loop* L, uint64_t frame_id, float* slopes, size_t ns, float* cmds, size_t na,
+                      int64_t timeout_us) {
+    if (!L) return fail(nullptr, RTC_EINVAL, "loop is NULL");
+    if (slopes && (ns != (size_t)L->ns || !L->telemetry)) return fail(L, RTC_EINVAL, "slopes need ns floats and RTC_FLAG_TELEMETRY");
+    if (cmds && na != (size_t)L->na) return fail(L, RTC_EINVAL, "cmds must hold na floats");
+    TRY(use_device(L));
+    const int slot = find_slot(L, frame_id);
+    if (slot < 0) return fail(L, RTC_ENOENT, "frame not in the ring");
+    const auto deadline = deadline_of(timeout_us);
+    TRY(wait_event(L, L->slots[slot].ev_final, deadline, timeout_us < 0));
+    TRY(wait_event(L, L->slots[slot].ev_tel, deadline, timeout_us < 0));
+    std::lock_guard<std::mutex> g(L->mu);
+    if (!L->slots[slot].used || L->slots[slot].frame_id != frame_id) return fail(L, RTC_ENOENT, "frame left the ring");
+    const float* base = L->h_ring + (size_t)slot * L->slot_floats;
+    if (cmds) std::memcpy(cmds, base, (size_t)L->na * 4);
+    if (slopes) std::memcpy(slopes, base + round_up((size_t)L->na, 4), (size_t)L->ns * 4);
+    return RTC_OK;
+}
+
+int rtc_get_timing(rtc_loop* L, uint64_t frame_id, rtc_timing* out, int64_t timeout_us) {
+    if (!L || !out) return fail(L, RTC_EINVAL, "loop and out are required");
+    if (!L->timing) return fail(L, RTC_EINVAL, "loop created without RTC_FLAG_TIMING");
+    TRY(use_device(L));
+    const int slot = find_slot(L, frame_id);
+    if (slot < 0) return fail(L, RTC_ENOENT, "frame not in the ring");
+    const Slot& s = L->slots[slot];
+    const auto deadline = deadline_of(timeout_us);
+    TRY(wait_event(L, s.ev_polc, deadline, timeout_us < 0));
+    out->frame_id = frame_id;
+    out->slopes_us = elapsed(s.ev_tail, s.ev_slopes);
+    out->mvm_us = elapsed(s.ev_slopes, s.ev_mvm);
+    out->final_us = elapsed(s.ev_mvm, s.ev_final);
+    out->polc_us = elapsed(s.ev_final, s.ev_polc);
+    out->latency_us = elapsed(s.ev_tail, s.ev_final);
+    out->frame_us = elapsed(s.ev_start, s.ev_final);
+    return RTC_OK;
+}
+
+int rtc_get_state(rtc_loop* L, float* a, size_t na) {
+    if (!L || !a || na != (size_t)L->na) return fail(L, RTC_EINVAL, "a must hold na floats");
+    TRY(use_device(L));
+    CK(L, cudaStreamSynchronize(L->st));
+    CK(L, cudaMemcpy(a, L->d_a, na * 4, cudaMemcpyDeviceToHost));
+    return RTC_OK;
+}
+
+int rtc_set_state(rtc_loop* L, const float* a, size_t na) {
+    if (!L || !a || na != (size_t)L->na) return fail(L, RTC_EINVAL, "a must hold na floats");
+    if (!all_finite(a, na)) return fail(L, RTC_EINVAL, "state not finite");
+    TRY(use_device(L));
+    CK(L, cudaStreamSynchronize(L->st));
+    CK(L, cudaMemcpy(L->d_a, a, na * 4, cudaMemcpyHostToDevice));
+    if (L->has_polc)
+        CK(L, launch_gemv(L->p_dtype, L->d_P, L->d_pblock, 0, 1, L->na, L->d_a, L->d_Pscale, L->d_q, 0, L->st));
+    CK(L, cudaStreamSynchronize(L->st));
+    return RTC_OK;
+}
+
+int rtc_sync(rtc_loop* L) {
+    if (!L) return fail(nullptr, RTC_EINVAL, "loop is NULL");
+    TRY(use_device(L));
+    CK(L, cudaStreamSynchronize(L->st));
+    CK(L, cudaStreamSynchronize(L->st_tel));
+    return RTC_OK;
+}
+
+int rtc_get_stream(rtc_loop* L, void** stream) {
+    if (!L || !stream) return fail(L, RTC_EINVAL, "loop and stream are required");
+    *stream = static_cast<void*>(L->st);
+    return RTC_OK;
+}
+
+int rtc_get_info(rtc_loop* L, rtc_info* out) {
+    if (!L || !out) return fail(L, RTC_EINVAL, "loop and out are required");
+    out->na = L->na;
+    out->ns = L->ns;
+    out->nwfs = L->nwfs;
+    out->nblocks = L->nblk;
+    out->nrows = L->nrows;
+    out->m_dtype = L->m_dtype;
+    out->p_dtype = L->p_dtype;
+    out->m_bytes = L->m_bytes;
+    out->p_bytes = L->p_bytes;
+    out->pixel_bytes = L->pixel_bytes;
+    out->device_bytes = L->device_bytes;
+    std::lock_guard<std::mutex> g(L->mu);
+    out->frames_done = L->frames_done;
+    out->frames_dropped = L->frames_dropped;
+    out->frames_overrun = L->frames_overrun;
+    return RTC_OK;
+}
+
+const char* rtc_last_error(const rtc_loop* L) { return L ? L->err.c_str() : g_err.c_str(); }
+
+int rtc_quantize_rows(int32_t dtype, int32_t na, int32_t ns, const float* M, size_t ld, void* codes, float* scale,
+                      void* stream) {
+    if ((dtype != RTC_BF16 && dtype != RTC_E4M3) || na < 0 || ns < 0 || ld < (size_t)ns)
+        return fail(nullptr, RTC_EINVAL, "bad quantize arguments");
+    if (na == 0) return RTC_OK;
+    if (!M || !codes || !scale) return fail(nullptr, RTC_EINVAL, "NULL pointer");
+    cudaError_t e = launch_quantize(dtype, na, ns, M, ld, codes, scale, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "quantize kernel");
+    return RTC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,58 @@
+"""The C-ABI library loads and exports every entry point include/rtc.h declares
+(CPU only: no call here reaches the GPU)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rtc.h")
+
+
+def declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(rtc_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared()
+    for n in ("rtc_create", "rtc_submit_pixels", "rtc_get_commands", "rtc_destroy", "rtc_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(rtc):
+    missing = [n for n in declared() if not hasattr(rtc.lib, n)]
+    assert not missing
+    assert sorted(n for n, _, _ in rtc.SIGNATURES) == declared()
+
+
+def test_create_rejects_null_and_bad_geometry_without_gpu(rtc):
+    h = C.c_void_p()
+    assert rtc.lib.rtc_create(None, None, None, None, C.byref(h)) == rtc.RTC_EINVAL
+    assert h.value is None
+    assert b"required" in rtc.lib.rtc_last_error(None)
+    w = (rtc.rtc_wfs * 1)()
+    w[0].kind, w[0].width, w[0].height = rtc.RTC_WFS_SH, 16, 16
+    w[0].nsubx = w[0].nsuby = 3
+    w[0].npx, w[0].nblocks = 8, 1          # 3 x 8 = 24 > 16: grid outside the frame
+    geo = rtc.rtc_geometry(1, w, 0, 0, 4)
+    cm = rtc.rtc_cmat(1, 18, rtc.RTC_F32, C.c_void_p(1), None)
+    pol = rtc.rtc_polc(None, 0, None, 0.5, 0.01, None, 0, 0.0, 0.0)
+    assert rtc.lib.rtc_create(C.byref(geo), None, C.byref(cm), C.byref(pol), C.byref(h)) == rtc.RTC_EINVAL
+    assert b"outside the frame" in rtc.lib.rtc_last_error(None)
+    w[0].npx, w[0].nblocks = 4, 5          # more blocks than subaperture rows
+    assert rtc.lib.rtc_create(C.byref(geo), None, C.byref(cm), C.byref(pol), C.byref(h)) == rtc.RTC_EINVAL
+
+
+def test_quantize_rejects_bad_arguments_without_gpu(rtc):
+    assert rtc.lib.rtc_quantize_rows(rtc.RTC_F32, 2, 2, None, 2, None, None, None) == rtc.RTC_EINVAL
+    assert rtc.lib.rtc_quantize_rows(rtc.RTC_BF16, 2, 4, None, 2, None, None, None) == rtc.RTC_EINVAL
+    assert rtc.lib.rtc_quantize_rows(rtc.RTC_BF16, 0, 4, None, 4, None, None, None) == rtc.RTC_OK
+
+
+def test_null_loop_calls_are_rejected(rtc):
+    assert rtc.lib.rtc_submit_pixels(None, None) == rtc.RTC_EINVAL
+    assert rtc.lib.rtc_destroy(None) == rtc.RTC_OK
+    assert rtc.lib.rtc_last_error(None) is not None

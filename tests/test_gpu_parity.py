@@ -1,0 +1,293 @@
+"""CUDA path against the FP64 oracle, element by element, through the C ABI."""
+import copy
+
+import numpy as np
+import pytest
+
+from oracle import OracleLoop, quantize_rows
+from paper_1903_01852_gb300 import synth
+from parity_util import TOL_F32, WAIT_US, device_frames, rel, run_pair
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    assert torch.cuda.is_available()
+    return torch
+
+
+# ------------------------------------------------------------------ small SH loop
+
+def test_scao_small_chunked_multi_frame(rtc, torch_cuda):
+    cfg = synth.make_config("scao_small", nblocks=4)
+    frames = synth.draw_frames(cfg, 12, seed=21)
+    with rtc.Loop(cfg, telemetry=True) as loop:
+        errs, _ = run_pair(loop, cfg, frames, nchunks=4)
+    assert max(e[1] for e in errs) <= TOL_F32
+
+
+def test_device_resident_frame_equals_chunked_bitwise(rtc, torch_cuda):
+    cfg = synth.make_config("scao_small", nblocks=3)
+    frames = synth.draw_frames(cfg, 5, seed=22)
+    with rtc.Loop(cfg, telemetry=True) as a, rtc.Loop(cfg, telemetry=True) as b, \
+            rtc.Loop(cfg, telemetry=True) as c:
+        _, ca = run_pair(a, cfg, frames, mode="chunked", nchunks=5)
+        _, cb = run_pair(b, cfg, frames, mode="device")
+        _, cc = run_pair(c, cfg, frames, mode="chunked", nchunks=1)
+    for x, y, z in zip(ca, cb, cc):
+        assert np.array_equal(x, y) and np.array_equal(x, z)
+
+
+def test_threshold_clip_mode_and_reference_slopes(rtc, torch_cuda):
+    cfg = synth.make_config("scao_small", with_ref=True, nblocks=2)
+    cfg["wfs"][0]["thresh_mode"] = "clip"
+    frames = synth.draw_frames(cfg, 4, seed=23)
+    with rtc.Loop(cfg, telemetry=True) as loop:
+        run_pair(loop, cfg, frames, nchunks=3)
+
+
+def test_clip_of_commands(rtc, torch_cuda):
+    cfg = synth.make_config("scao_small")
+    cfg["M"] = cfg["M"] * np.float32(50.0)
+    cfg["clip"] = (-0.05, 0.04)
+    frames = synth.draw_frames(cfg, 4, seed=24)
+    with rtc.Loop(cfg, telemetry=True) as loop:
+        _, cmds = run_pair(loop, cfg, frames)
+    assert max(c.max() for c in cmds) == np.float32(0.04) and min(c.min() for c in cmds) == np.float32(-0.05)
+
+
+def test_zero_flux_frame_gives_minus_reference(rtc, torch_cuda):
+    cfg = synth.make_config("scao_small", with_ref=True)
+    dark = [np.zeros((128, 128), np.uint16)]
+    with rtc.Loop(cfg, telemetry=True) as loop:
+        loop.submit_frame(1, dark)
+        fid, a = loop.get_commands(timeout_us=WAIT_US)
+        s, _ = loop.get_telemetry(fid, timeout_us=WAIT_US)
+    assert np.array_equal(s, -cfg["ref_slopes"])
+    assert np.all(np.isfinite(a))
+
+
+# ------------------------------------------------------------------ ragged geometry
+
+def ragged_config(seed=31):
+    rng = np.random.default_rng(seed)
+    w1 = synth.sh_wfs(rng, 7, 5, 45, 39, 0.3, ox=3, oy=2, nblocks=3)       # odd origin, width not /8, npx 5
+    w1["valid"][3, :] = 0                                                  # a subaperture row with no valid unit
+    w2 = synth.pyramid_wfs(rng, 13, 37, 34, 0.0, qx=[1, 19, 2, 20], qy=[0, 1, 17, 18], nblocks=5)
+    w3 = synth.sh_wfs(rng, 2, 13, 30, 29, 0.0, ox=1, oy=3, nblocks=2)      # two wide subapertures
+    w4 = synth.sh_wfs(rng, 1, 3, 3, 3, 0.0, nblocks=1)                    # a single 3x3 subaperture
+    wfs = [w1, w2, w3, w4]
+    ns = sum(2 * synth.num_valid(w) for w in wfs)
+    na = 37
+    return dict(name="ragged", na=na, ns=ns, wfs=wfs, M=synth.control_matrix(rng, na, ns, sd=1e-2),
+                M_scale=None, M_dtype="f32", P=synth.polc_matrix(rng, na), P_scale=None, P_dtype="f32",
+                gain=0.4, leak=0.02, clip=None, a0=rng.normal(0, 0.1, na).astype(np.float32),
+                ref_slopes=rng.normal(0, 0.1, ns).astype(np.float32))
+
+
+@pytest.mark.parametrize("nchunks", [1, 3, 7])
+def test_ragged_geometry_and_chunking(rtc, torch_cuda, nchunks):
+    cfg = ragged_config()
+    frames = synth.draw_frames(cfg, 4, seed=32)
+    with rtc.Loop(cfg, telemetry=True) as loop:
+        run_pair(loop, cfg, frames, nchunks=nchunks)
+
+
+def test_ragged_row_by_row_equals_whole_frame_bitwise(rtc, torch_cuda):
+    cfg = ragged_config()
+    frames = synth.draw_frames(cfg, 3, seed=33)
+    outs = []
+    for plans in ("rows", "whole"):
+        with rtc.Loop(cfg, telemetry=True) as loop:
+            cm = []
+            for k, f in enumerate(frames):
+                p = [[(r, r + 1) for r in range(x.shape[0])] for x in f] if plans == "rows" else None
+                loop.submit_frame(k + 1, f, p)
+                cm.append(loop.get_commands(timeout_us=WAIT_US)[1])
+            outs.append(cm)
+    assert all(np.array_equal(x, y) for x, y in zip(*outs))
+
+
+# ------------------------------------------------------------------ POLC
+
+def test_implicit_polc_on_gpu_equals_explicit_polc(rtc, torch_cuda):
+    from oracle import rtc_oracle as orc
+    cfg = synth.make_config("scao_small")
+    rng = np.random.default_rng(41)
+    na, ns = cfg["na"], cfg["ns"]
+    D = (rng.standard_normal((ns, na)) * 0.02).astype(np.float32)
+    P = (cfg["M"].astype(np.float64) @ D.astype(np.float64) - np.eye(na)).astype(np.float32)
+    cfg["P"] = P
+    frames = synth.draw_frames(cfg, 6, seed=42)
+    m64, d64 = cfg["M"].astype(np.float64), D.astype(np.float64)
+    a_exp = np.zeros(na)
+    # P stored in float32 differs from M D - I by rounding; compare both to the oracle's implicit form
+    # on the stored P (tight) and to the explicit form on the exact M, D (float32-rounding level)
+    with rtc.Loop(cfg, telemetry=True) as loop:
+        _, cmds = run_pair(loop, cfg, frames)
+    for f, a in zip(frames, cmds):
+        s = orc.frame_slopes(cfg, f)
+        a_exp = orc.explicit_polc_step(m64, d64, s, a_exp, cfg["gain"], cfg["leak"])
+        assert rel(a, a_exp) <= 1e-5
+
+
+# ------------------------------------------------------------------ quantised matrices
+
+@pytest.mark.parametrize("fmt", ["bf16", "e4m3"])
+def test_quantize_rows_bit_exact_against_oracle(rtc, torch_cuda, fmt):
+    torch = torch_cuda
+    rng = np.random.default_rng(51)
+    M = (rng.standard_normal((67, 1003)) * 10.0 ** rng.uniform(-6, 1, size=(67, 1))).astype(np.float32)
+    M[5] = 0.0
+    M[7, :10] = [1e-30, -1e-30, 448.0, 3e-3, 0.5, -0.5, 1.0, 0.0, -0.0, 2.0]
+    codes, scale = rtc.quantize_rows(torch.from_numpy(M).cuda(), fmt)
+    torch.cuda.synchronize()
+    c_ref, s_ref = quantize_rows(M, fmt)
+    got = codes.cpu().numpy().view(np.uint16 if fmt == "bf16" else np.uint8)
+    assert np.array_equal(scale.cpu().numpy(), s_ref)
+    assert np.array_equal(got, c_ref)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "e4m3"])
+def test_quantised_loop_parity(rtc, torch_cuda, fmt):
+    cfg = ragged_config(seed=52)
+    codes, scale = quantize_rows(cfg["M"], fmt)
+    pc, ps = quantize_rows(cfg["P"], fmt)
+    cfg.update(M=codes, M_scale=scale, M_dtype=fmt, P=pc, P_scale=ps, P_dtype=fmt)
+    frames = synth.draw_frames(cfg, 4, seed=53)
+    with rtc.Loop(cfg, telemetry=True) as loop:
+        run_pair(loop, cfg, frames, nchunks=3)
+
+
+# ------------------------------------------------------------------ protocol and state
+
+def test_order_errors_and_dropped_frames(rtc, torch_cuda):
+    cfg = synth.make_config("scao_small", nblocks=2)
+    frames = synth.draw_frames(cfg, 4, seed=61)
+    ref = OracleLoop(cfg)
+    with rtc.Loop(cfg, telemetry=True) as loop:
+        f = frames[0][0]
+        assert loop.submit(10, 0, 0, 64, f[:64]) == rtc.RTC_OK
+        with pytest.raises(rtc.RtcError) as e:
+            loop.submit(10, 0, 70, 128, f[70:])                  # gap in the rows
+        assert e.value.code == rtc.RTC_EORDER
+        with pytest.raises(rtc.RtcError) as e:
+            loop.submit(9, 0, 0, 128, f)                         # older frame id
+        assert e.value.code == rtc.RTC_EORDER
+        assert loop.submit(11, 0, 0, 128, frames[1][0]) == rtc.RTC_EDROPPED   # frame 10 dropped
+        fid, a = loop.get_commands(timeout_us=WAIT_US)
+        assert fid == 11
+        ref.step(frames[1])
+        with pytest.raises(rtc.RtcError) as e:
+            loop.submit(11, 0, 0, 128, frames[2][0])             # repeated id of a completed frame
+        assert e.value.code == rtc.RTC_EORDER
+        loop.submit_frame(12, frames[2])
+        fid, a = loop.get_commands(timeout_us=WAIT_US)
+        _, a_ref = ref.step(frames[2])
+        assert fid == 12 and rel(a, a_ref) <= TOL_F32
+        assert loop.info()["frames_dropped"] == 1
+
+
+def test_get_commands_times_out_when_nothing_pending(rtc, torch_cuda):
+    cfg = synth.make_config("scao_small")
+    with rtc.Loop(cfg) as loop:
+        with pytest.raises(TimeoutError):
+            loop.get_commands(timeout_us=2000)
+
+
+def test_state_checkpoint_resume(rtc, torch_cuda):
+    cfg = ragged_config(seed=71)
+    frames = synth.draw_frames(cfg, 6, seed=72)
+    with rtc.Loop(cfg, telemetry=True) as a:
+        _, ca = run_pair(a, cfg, frames)
+    with rtc.Loop(cfg, telemetry=True) as b:
+        for k in range(3):
+            b.submit_frame(k + 1, frames[k])
+            b.get_commands(timeout_us=WAIT_US)
+        st = b.get_state()
+    with rtc.Loop(cfg, telemetry=True) as c:
+        c.set_state(st)
+        for k in range(3, 6):
+            c.submit_frame(k + 1, frames[k])
+            assert np.array_equal(c.get_commands(timeout_us=WAIT_US)[1], ca[k])
+
+
+def test_ring_overrun_and_missing_telemetry(rtc, torch_cuda):
+    cfg = synth.make_config("scao_small")
+    frames = synth.draw_frames(cfg, 6, seed=81)
+    with rtc.Loop(cfg, telemetry=True, ring=2) as loop:
+        for k, f in enumerate(frames):
+            loop.submit_frame(k + 1, f)
+        loop.sync()
+        with pytest.raises(rtc.RtcError) as e:
+            loop.get_telemetry(1)
+        assert e.value.code == rtc.RTC_ENOENT
+        fid, _ = loop.get_commands(timeout_us=WAIT_US)
+        assert fid == 5
+        assert loop.info()["frames_overrun"] == 4
+
+
+def test_nan_in_calibration_map_is_rejected(rtc, torch_cuda):
+    cfg = synth.make_config("scao_small")
+    cfg["wfs"][0]["flat"] = cfg["wfs"][0]["flat"].copy()
+    cfg["wfs"][0]["flat"][3, 4] = np.nan
+    with pytest.raises(rtc.RtcError) as e:
+        rtc.Loop(cfg)
+    assert e.value.code == rtc.RTC_EINVAL
+
+
+def test_pinned_host_chunks(rtc, torch_cuda):
+    torch = torch_cuda
+    cfg = synth.make_config("scao_small", nblocks=4)
+    frames = synth.draw_frames(cfg, 3, seed=91)
+    ref = OracleLoop(cfg)
+    pinned = torch.empty((128, 128), dtype=torch.int16, pin_memory=True)
+    with rtc.Loop(cfg, telemetry=True) as loop:
+        for k, f in enumerate(frames):
+            pinned.numpy()[:] = f[0].view(np.int16)
+            for r0, r1 in synth.chunk_plan(cfg["wfs"][0], 4):
+                loop.submit(k + 1, 0, r0, r1, pinned[r0:r1])
+            fid, a = loop.get_commands(timeout_us=WAIT_US)
+            _, a_ref = ref.step(f)
+            assert rel(a, a_ref) <= TOL_F32
+
+
+# ------------------------------------------------------------------ full-size configurations
+
+@pytest.mark.parametrize("name,nframes", [("elt_scao_sh", 3), ("elt_scao_pyramid", 3)])
+def test_full_size_scao(rtc, torch_cuda, name, nframes):
+    cfg = synth.make_config(name)
+    frames = synth.draw_frames(cfg, nframes, seed=101)
+    with rtc.Loop(cfg, telemetry=True) as loop:
+        run_pair(loop, cfg, frames, nchunks=8)
+
+
+@pytest.fixture(scope="module")
+def mcao():
+    cfg = synth.make_config("mcao")
+    return cfg, synth.draw_frames(cfg, 2, seed=111)
+
+
+def test_full_size_mcao_fp32_with_polc(rtc, torch_cuda, mcao):
+    cfg, frames = mcao
+    with rtc.Loop(cfg, telemetry=True) as loop:
+        errs, _ = run_pair(loop, cfg, frames, mode="device")
+    print("mcao fp32 errors (slopes, commands):", errs)
+
+
+def test_full_size_mcao_bf16_against_stored_and_true_matrix(rtc, torch_cuda, mcao):
+    torch = torch_cuda
+    cfg, frames = mcao
+    q = copy.copy(cfg)
+    codes, scale = rtc.quantize_rows(torch.from_numpy(cfg["M"]).cuda(), "bf16")
+    pc, ps = rtc.quantize_rows(torch.from_numpy(cfg["P"]).cuda(), "bf16")
+    q.update(M=codes.cpu().numpy().view(np.uint16), M_scale=scale.cpu().numpy(), M_dtype="bf16",
+             P=pc.cpu().numpy().view(np.uint16), P_scale=ps.cpu().numpy(), P_dtype="bf16")
+    with rtc.Loop(q, telemetry=True) as loop:
+        errs, cmds = run_pair(loop, q, frames, mode="device", nchunks=8)
+    ref = OracleLoop(cfg)
+    true_err = [rel(a, ref.step(f)[1]) for f, a in zip(frames, cmds)]
+    print("mcao bf16 errors vs stored matrix:", errs, "vs float32 matrix:", true_err)
+    assert max(true_err) < 2.0 ** -8 * 8
