@@ -270,6 +270,36 @@ const char* rtc_last_error(const rtc_loop* loop);
 int rtc_quantize_rows(int32_t dtype, int32_t na, int32_t ns, const float* M, size_t ld,
                       void* codes, float* scale, void* stream);
 
+/* ---- allocation-free reconstruction step ------------------------------ */
+
+/* Floats in the library's fixed scratch array used by rtc_reconstruct_noalloc
+ * (8 MiB on every GPU that loads the library, held until the process exits). */
+#define RTC_NOALLOC_MAX_FLOATS 2097152
+
+/* The paper has no counterpart to this entry point: it is here for callers
+ * that must not allocate device memory once running, such as a hard real-time
+ * control thread (cudaMalloc can synchronise the device and has no latency
+ * bound) or code hosted in a framework that owns every device allocation.
+ * It runs the reconstruction MVM and the leaky-integrator step of the loop on
+ * the caller's buffers without allocating anything:
+ *   a_out[r] = (1 - leak) a_in[r] + gain (row_scale[r] * sum_j M[r][j] s[j] + q[r])
+ * M: device float32, row r at M + r*ld (16-byte aligned, ld >= ns and a
+ * multiple of 4); s: device float32[ns] (16-byte aligned); row_scale and q:
+ * device float32[na] or NULL (1 and 0); a_in, a_out: device float32[na], may
+ * be the same buffer.  The partial sums of the column splits go to a static
+ * device array of RTC_NOALLOC_MAX_FLOATS floats; na larger than that returns
+ * RTC_EINVAL, as do NULL or misaligned pointers.  The first call on each
+ * device looks up that array's device address with the device current, so
+ * make one call on each device before any stream capture.  Every call shares
+ * the array: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on it and must be serialised by the caller.  Nothing in the
+ * array needs clearing: every call overwrites the part it reads.  stream: a
+ * cudaStream_t or NULL; asynchronous.  Returns RTC_ECUDA if a launch fails. */
+int rtc_reconstruct_noalloc(int32_t na, int32_t ns, const float* M, size_t ld,
+                            const float* row_scale, const float* s, const float* q,
+                            const float* a_in, float* a_out, float gain, float leak,
+                            void* stream);
+
 #ifdef __cplusplus
 }
 #endif

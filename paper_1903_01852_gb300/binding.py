@@ -96,6 +96,8 @@ SIGNATURES = [
     ("rtc_last_error", C.c_char_p, [C.c_void_p]),
     ("rtc_quantize_rows", C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_size_t, C.c_void_p,
                                     C.c_void_p, C.c_void_p]),
+    ("rtc_reconstruct_noalloc", C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_float, C.c_float, C.c_void_p]),
 ]
 
 
