@@ -148,9 +148,9 @@ def profiled_traffic():
 
 # ---------------------------------------------------------------------------- workload
 
-def make_workload(seed_frames=1):
+def make_workload(seed_frames=1, name="mcao"):
     from paper_1903_01852_gb300 import synth
-    cfg = synth.make_config("mcao")
+    cfg = synth.make_config(name)
     frames = synth.draw_frames(cfg, FRAME_RING, seed=seed_frames)
     return cfg, frames
 
@@ -168,11 +168,13 @@ def bf16_config(cfg, rtc, torch):
 
 
 def mvm_bytes(info, cfg):
-    """Algorithmic bytes of one reconstruction MVM launch: matrix (true size), its row
-    scales, the slopes read and the per-block partial commands written."""
+    """Algorithmic bytes of one reconstruction MVM launch with its fused finalisation:
+    matrix (true size) and row scales, the slopes read, the per-block partial commands
+    written and read back, and q, a (read and write) and the commands written."""
     b = {"f32": 4, "bf16": 2, "e4m3": 1}[cfg.get("M_dtype", "f32")]
     na, ns = info["na"], info["ns"]
-    return na * ns * b + (4 * na if cfg.get("M_scale") is not None else 0) + 4 * ns + 4 * na * info["nblocks"]
+    return (na * ns * b + (4 * na if cfg.get("M_scale") is not None else 0) + 4 * ns
+            + 2 * 4 * na * info["nblocks"] + 4 * 4 * na)
 
 
 def run_unpaced(loop, dev_frames, steps, warmup, torch, sampler, first_id):
@@ -336,7 +338,9 @@ def ours_arm(args, world, rank, local):
 
     torch.cuda.set_device(local)
     peak, peak_kind = peaks()
-    cfg, frames = make_workload()
+    cfg, frames = make_workload(name=args.workload)
+    if args.quick:
+        return quick_arm(args, cfg, frames, rtc, torch, local)
     dev_frames = []
     for f in frames:
         per = []
@@ -456,6 +460,27 @@ def ours_arm(args, world, rank, local):
     print(json.dumps(res), flush=True)
 
 
+def quick_arm(args, cfg, frames, rtc, torch, local):
+    """Profiling aid: only the unpaced, HBM-resident float32 loop on the chosen workload."""
+    dev_frames = []
+    for f in frames:
+        per = []
+        for x in f:
+            h, w = x.shape
+            t = torch.zeros((h, (w + 7) // 8 * 8), dtype=torch.int16, device="cuda")
+            t[:, :w] = torch.from_numpy(x.view(np.int16)).cuda()
+            per.append(t[:, :w])
+        dev_frames.append(per)
+    sampler = ClockSampler(local)
+    with rtc.Loop(cfg, device=local, timing=True, telemetry=True) as loop:
+        rows, _ = run_unpaced_timed(loop, dev_frames, args.steps, args.warmup, sampler, 1)
+        info = loop.info()
+    lat = stats([r["latency_us"] for r in rows])
+    mvm = statistics.median([r["mvm_us"] for r in rows])
+    print(json.dumps({"workload": args.workload, "quick": True, "latency_us": lat, "mvm_us": mvm,
+                      "mvm_gbs": mvm_bytes(info, cfg) / (mvm * 1e-6) / 1e9}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -463,6 +488,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--workload", default="mcao", help="configuration (profiling aid; the bench line is mcao)")
+    ap.add_argument("--quick", action="store_true", help="profiling aid: only the unpaced float32 loop")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -36,6 +36,31 @@ struct SlopeRow {
     int nunits;               // valid units in this row
     int s_pad;                // padded slope-buffer index of the row's first slope
     int s_compact;            // compact slope index of the row's first slope
+    int nparts;               // CTAs sharing this row (split by pixel rows)
+    int pscr;                 // float offset of this row's per-part sums (nparts > 1)
+};
+
+// One CTA of the slope kernel: pixel rows [pr0, pr1) of a subaperture row.
+struct SlopePart {
+    int row;                  // slope-row table index
+    int part;                 // part index within the row
+    int pr0, pr1;             // pixel rows within the subaperture (SH); unused for pyramid rows
+};
+
+constexpr int kFinRows = 32;  // rows per finalisation tile of the fused MVM tail
+
+// Fused finalisation of the reconstruction MVM (enabled for the control matrix).
+struct FinaliseArgs {
+    int enabled;
+    int nblk;                 // column blocks per frame
+    unsigned* counters;       // per finalisation tile: rows done, summed over blocks
+    const float* scale;       // control-matrix row scale or NULL
+    const float* q;           // POLC term from the previous frame
+    float* a;                 // integrator state
+    float* cmd;               // commands (page-locked ring slot, mapped)
+    float oml, gain;          // 1 - leak, gain
+    int clip;
+    float amin, amax;
 };
 
 // Frame pointers for one launch; pitch in uint16 elements.
@@ -59,22 +84,18 @@ int elems_per_16B(int dtype);
 // Opt the slope kernel in to more than 48 KB of dynamic shared memory when needed.
 cudaError_t configure_slopes(int smem_bytes);
 
-// Slope kernel over table rows [row0, row0 + nrows).
-cudaError_t launch_slopes(const SlopeRow* rows, int row0, int nrows, const WfsDev* wfs,
-                          const FramePtrs& fp, const uint16_t* xlist, const float* ref,
-                          float* s_pad, int smem_bytes, cudaStream_t st);
+// Slope kernel over the part table entries [part0, part0 + nparts).
+cudaError_t launch_slopes(const SlopePart* parts, int part0, int nparts, const SlopeRow* rows,
+                          const WfsDev* wfs, const FramePtrs& fp, const uint16_t* xlist,
+                          const float* ref, float* s_pad, float* pscr, unsigned* counters,
+                          int smem_bytes, cudaStream_t st);
 
 // GEMV over blocks [b0, b0 + nb): out[b * out_stride + r] = sum_j M_b[r][j] x[x_off_b + j],
-// times out_scale[r] when out_scale is not NULL.
+// times out_scale[r] when out_scale is not NULL; with fin, the CTA completing the
+// last block of a row tile also finalises it (a, cmd).
 cudaError_t launch_gemv(int dtype, const void* M, const BlockDev* blocks, int b0, int nb,
                         int na, const float* x, const float* out_scale, float* out,
-                        long long out_stride, cudaStream_t st);
-
-// Finalise: y = sum_b partial[b][r] (b ascending), times scale; w = y + q;
-// a = (1 - leak) a + gain w; optional clip; writes a and cmd.
-cudaError_t launch_finalise(const float* partial, int nblk, int na, const float* scale,
-                            const float* q, float* a, float* cmd, float one_minus_leak,
-                            float gain, int clip, float amin, float amax, cudaStream_t st);
+                        long long out_stride, const FinaliseArgs* fin, cudaStream_t st);
 
 // Telemetry: compact copy of the padded slope buffer, block by block.
 cudaError_t launch_pack_slopes(const BlockDev* blocks, int nblk, int max_cols,

@@ -1,11 +1,13 @@
 // CUDA kernels of the AO real-time-control hot path (sm_103a).
 //
 //   slopes_kernel    calibration fused with SH centre of gravity / pyramid quad
-//                    difference, one CTA per slope row (Section 2.2, Fig. wfs_slopes)
+//                    difference, one CTA per part of a slope row (Section 2.2,
+//                    Fig. wfs_slopes)
 //   gemv_kernel      reconstruction MVM, one partial per column block, warp per
 //                    matrix row, 128-bit streaming loads (Section 2.3: the MVM
-//                    is memory-bandwidth bound); also the POLC product P a
-//   finalise_kernel  partial sums + POLC term + leaky integrator (Section 3, 3.4)
+//                    is memory-bandwidth bound), with the finalisation (partial
+//                    sums + POLC term + leaky integrator, Section 3 and 3.4)
+//                    fused into its tail; also the POLC product P a
 //   pack / relayout / quantize / check kernels used at creation and for telemetry
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -18,6 +20,12 @@ namespace rtc {
 size_t dtype_size(int dtype) { return dtype == RTC_F32 ? 4 : dtype == RTC_BF16 ? 2 : 1; }
 int elems_per_16B(int dtype) { return int(16 / dtype_size(dtype)); }
 
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // ---------------------------------------------------------------------------
 // Calibration: c = (raw - dark) * flat in float32 (both operations rounded to
 // nearest, never contracted), then the threshold.  A pixel is lit iff c > T.
@@ -28,23 +36,32 @@ __device__ __forceinline__ float calibrate(unsigned raw, float dark, float flat,
     return mode == RTC_THRESH_SUBTRACT ? __fsub_rn(c, T) : c;
 }
 
-// SH slope row: the CTA first reduces each pixel column of the subaperture
-// strip over its npx rows (column flux F_c and first moment in y), split in
-// `groups` row groups so narrow strips still use the whole CTA; then one
-// thread per valid subaperture adds its npx columns.
-__device__ void sh_row(const SlopeRow& row, const WfsDev& W, const uint16_t* __restrict__ px,
-                       long long pitch, const uint16_t* __restrict__ xlist,
-                       const float* __restrict__ ref, float* __restrict__ s_pad, float* sm) {
+// SH slope-row part: pixel rows [pr0, pr1) of one subaperture row.  The CTA
+// first reduces each pixel column of the strip over its rows (column flux F_c
+// and first moment in y), in G row groups so that narrow strips still use the
+// whole CTA, four rows of loads in flight per thread; then each valid
+// subaperture adds its npx columns (one thread per subaperture when that sum is
+// short, one warp otherwise).  A row split in several parts (large
+// subapertures) publishes per-part sums; the last part to finish adds them in
+// part order and writes the slopes.  Every sum has a fixed order.
+__device__ void sh_part(const SlopePart& P, const SlopeRow& row, const WfsDev& W, const uint16_t* __restrict__ px,
+                        long long pitch, const uint16_t* __restrict__ xlist, const float* __restrict__ ref,
+                        float* __restrict__ s_pad, float* __restrict__ pscr, unsigned* __restrict__ counters,
+                        float* sm) {
+    __shared__ int s_last;
     const int n = W.npx;
     const int ws = W.nsubx * n;                 // strip width in pixels
     const int x0 = W.ox;
     const int y0 = W.oy + row.row * n;
     const int q0 = x0 >> 2;                     // quads of 4 pixels aligned to absolute columns
     const int nq = ((x0 + ws + 3) >> 2) - q0;
-    const int G = W.sh_groups;
+    const int nr = P.pr1 - P.pr0;
+    const int G = max(1, min(nr, (int)blockDim.x / nq));
     float* colF = sm;                           // [G][ws]
     float* colY = sm + G * ws;                  // [G][ws]
     const float half = 0.5f * float(n - 1);
+    const float T = W.threshold;
+    const int mode = W.thresh_mode;
 
     for (int idx = threadIdx.x; idx < nq * G; idx += blockDim.x) {
         const int q = idx % nq;
@@ -52,17 +69,39 @@ __device__ void sh_row(const SlopeRow& row, const WfsDev& W, const uint16_t* __r
         const int xa = (q0 + q) << 2;
         float F[4] = {0.f, 0.f, 0.f, 0.f};
         float Y[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 2
-        for (int r = g; r < n; r += G) {
-            const int yy = y0 + r;
+        int r = P.pr0 + g;
+        for (; r + 3 * G < P.pr1; r += 4 * G) {
+            uint2 rw[4];
+            float4 d[4], f[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const long long yy = y0 + r + k * G;
+                rw[k] = __ldg(reinterpret_cast<const uint2*>(px + yy * pitch + xa));
+                d[k] = __ldg(reinterpret_cast<const float4*>(W.dark + yy * W.calib_pitch + xa));
+                f[k] = __ldg(reinterpret_cast<const float4*>(W.flat + yy * W.calib_pitch + xa));
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float yc = float(r + k * G) - half;
+                const float t0 = calibrate(rw[k].x & 0xffffu, d[k].x, f[k].x, T, mode);
+                const float t1 = calibrate(rw[k].x >> 16, d[k].y, f[k].y, T, mode);
+                const float t2 = calibrate(rw[k].y & 0xffffu, d[k].z, f[k].z, T, mode);
+                const float t3 = calibrate(rw[k].y >> 16, d[k].w, f[k].w, T, mode);
+                F[0] += t0; F[1] += t1; F[2] += t2; F[3] += t3;
+                Y[0] = fmaf(t0, yc, Y[0]); Y[1] = fmaf(t1, yc, Y[1]);
+                Y[2] = fmaf(t2, yc, Y[2]); Y[3] = fmaf(t3, yc, Y[3]);
+            }
+        }
+        for (; r < P.pr1; r += G) {
+            const long long yy = y0 + r;
             const uint2 rw = __ldg(reinterpret_cast<const uint2*>(px + yy * pitch + xa));
-            const float4 d = __ldg(reinterpret_cast<const float4*>(W.dark + (size_t)yy * W.calib_pitch + xa));
-            const float4 f = __ldg(reinterpret_cast<const float4*>(W.flat + (size_t)yy * W.calib_pitch + xa));
+            const float4 d = __ldg(reinterpret_cast<const float4*>(W.dark + yy * W.calib_pitch + xa));
+            const float4 f = __ldg(reinterpret_cast<const float4*>(W.flat + yy * W.calib_pitch + xa));
             const float yc = float(r) - half;
-            const float t0 = calibrate(rw.x & 0xffffu, d.x, f.x, W.threshold, W.thresh_mode);
-            const float t1 = calibrate(rw.x >> 16, d.y, f.y, W.threshold, W.thresh_mode);
-            const float t2 = calibrate(rw.y & 0xffffu, d.z, f.z, W.threshold, W.thresh_mode);
-            const float t3 = calibrate(rw.y >> 16, d.w, f.w, W.threshold, W.thresh_mode);
+            const float t0 = calibrate(rw.x & 0xffffu, d.x, f.x, T, mode);
+            const float t1 = calibrate(rw.x >> 16, d.y, f.y, T, mode);
+            const float t2 = calibrate(rw.y & 0xffffu, d.z, f.z, T, mode);
+            const float t3 = calibrate(rw.y >> 16, d.w, f.w, T, mode);
             F[0] += t0; F[1] += t1; F[2] += t2; F[3] += t3;
             Y[0] = fmaf(t0, yc, Y[0]); Y[1] = fmaf(t1, yc, Y[1]);
             Y[2] = fmaf(t2, yc, Y[2]); Y[3] = fmaf(t3, yc, Y[3]);
@@ -74,15 +113,66 @@ __device__ void sh_row(const SlopeRow& row, const WfsDev& W, const uint16_t* __r
         }
     }
     __syncthreads();
+
+    const bool single = row.nparts == 1;
+    auto emit = [&](int u, float Fs, float Xs, float Ys) {
+        if (single) {
+            float sx = 0.f, sy = 0.f;
+            if (Fs > 0.f) { sx = Xs / Fs; sy = Ys / Fs; }
+            if (ref) { sx -= ref[row.s_compact + 2 * u]; sy -= ref[row.s_compact + 2 * u + 1]; }
+            s_pad[row.s_pad + 2 * u] = sx;
+            s_pad[row.s_pad + 2 * u + 1] = sy;
+        } else {
+            float* o = pscr + row.pscr + 3 * ((size_t)P.part * row.nunits + u);
+            o[0] = Fs; o[1] = Xs; o[2] = Ys;
+        }
+    };
+    if (n * G <= 64) {
+        for (int u = threadIdx.x; u < row.nunits; u += blockDim.x) {
+            const int cx = xlist[row.unit0 + u] * n;
+            float Fs = 0.f, Xs = 0.f, Ys = 0.f;
+            for (int k = 0; k < n; ++k) {
+                float fc = 0.f, yc = 0.f;
+                for (int g = 0; g < G; ++g) { fc += colF[g * ws + cx + k]; yc += colY[g * ws + cx + k]; }
+                Fs += fc;
+                Xs = fmaf(float(k) - half, fc, Xs);
+                Ys += yc;
+            }
+            emit(u, Fs, Xs, Ys);
+        }
+    } else {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int u = warp; u < row.nunits; u += nw) {
+            const int cx = xlist[row.unit0 + u] * n;
+            float Fs = 0.f, Xs = 0.f, Ys = 0.f;
+            for (int p = lane; p < n * G; p += 32) {
+                const int k = p % n, g = p / n;
+                const float fc = colF[g * ws + cx + k];
+                Fs += fc;
+                Xs = fmaf(float(k) - half, fc, Xs);
+                Ys += colY[g * ws + cx + k];
+            }
+            Fs = warp_sum(Fs);
+            Xs = warp_sum(Xs);
+            Ys = warp_sum(Ys);
+            if (lane == 0) emit(u, Fs, Xs, Ys);
+        }
+    }
+    if (single) return;
+    // last part of the row to finish adds the parts in order
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&counters[P.row], 1u) == (unsigned)(row.nparts - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
     for (int u = threadIdx.x; u < row.nunits; u += blockDim.x) {
-        const int cx = xlist[row.unit0 + u] * n;
         float Fs = 0.f, Xs = 0.f, Ys = 0.f;
-        for (int k = 0; k < n; ++k) {
-            float fc = 0.f, yc = 0.f;
-            for (int g = 0; g < G; ++g) { fc += colF[g * ws + cx + k]; yc += colY[g * ws + cx + k]; }
-            Fs += fc;
-            Xs = fmaf(float(k) - half, fc, Xs);
-            Ys += yc;
+        for (int k = 0; k < row.nparts; ++k) {
+            const float* o = pscr + row.pscr + 3 * ((size_t)k * row.nunits + u);
+            Fs += __ldcg(o);
+            Xs += __ldcg(o + 1);
+            Ys += __ldcg(o + 2);
         }
         float sx = 0.f, sy = 0.f;
         if (Fs > 0.f) { sx = Xs / Fs; sy = Ys / Fs; }
@@ -90,6 +180,7 @@ __device__ void sh_row(const SlopeRow& row, const WfsDev& W, const uint16_t* __r
         s_pad[row.s_pad + 2 * u] = sx;
         s_pad[row.s_pad + 2 * u + 1] = sy;
     }
+    if (threadIdx.x == 0) counters[P.row] = 0u;
 }
 
 // Pyramid slope row: one thread per valid pupil pixel reads the matching pixel
@@ -122,21 +213,25 @@ __device__ void pyr_row(const SlopeRow& row, const WfsDev& W, const uint16_t* __
 }
 
 struct SlopeArgs {
+    const SlopePart* parts;
+    int part0;
     const SlopeRow* rows;
-    int row0;
     const WfsDev* wfs;
     FramePtrs fp;
     const uint16_t* xlist;
     const float* ref;
     float* s_pad;
+    float* pscr;
+    unsigned* counters;
 };
 
 __global__ void __launch_bounds__(kSlopeThreads) slopes_kernel(const __grid_constant__ SlopeArgs a) {
     extern __shared__ float sm[];
-    const SlopeRow row = a.rows[a.row0 + blockIdx.x];
+    const SlopePart P = a.parts[a.part0 + blockIdx.x];
+    const SlopeRow row = a.rows[P.row];
     const WfsDev W = a.wfs[row.wfs];
     if (W.kind == RTC_WFS_SH)
-        sh_row(row, W, a.fp.px[row.wfs], a.fp.pitch[row.wfs], a.xlist, a.ref, a.s_pad, sm);
+        sh_part(P, row, W, a.fp.px[row.wfs], a.fp.pitch[row.wfs], a.xlist, a.ref, a.s_pad, a.pscr, a.counters, sm);
     else
         pyr_row(row, W, a.fp.px[row.wfs], a.fp.pitch[row.wfs], a.xlist, a.ref, a.s_pad);
 }
@@ -146,12 +241,12 @@ cudaError_t configure_slopes(int smem_bytes) {
     return cudaFuncSetAttribute(slopes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
 }
 
-cudaError_t launch_slopes(const SlopeRow* rows, int row0, int nrows, const WfsDev* wfs,
-                          const FramePtrs& fp, const uint16_t* xlist, const float* ref,
-                          float* s_pad, int smem_bytes, cudaStream_t st) {
-    if (nrows <= 0) return cudaSuccess;
-    SlopeArgs a{rows, row0, wfs, fp, xlist, ref, s_pad};
-    slopes_kernel<<<nrows, kSlopeThreads, smem_bytes, st>>>(a);
+cudaError_t launch_slopes(const SlopePart* parts, int part0, int nparts, const SlopeRow* rows, const WfsDev* wfs,
+                          const FramePtrs& fp, const uint16_t* xlist, const float* ref, float* s_pad, float* pscr,
+                          unsigned* counters, int smem_bytes, cudaStream_t st) {
+    if (nparts <= 0) return cudaSuccess;
+    SlopeArgs a{parts, part0, rows, wfs, fp, xlist, ref, s_pad, pscr, counters};
+    slopes_kernel<<<nparts, kSlopeThreads, smem_bytes, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -228,12 +323,6 @@ __device__ __forceinline__ float dot16(const uint4& m, const float* x, int v, fl
     else return dot_e4m3(m, xp, acc);
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 struct GemvArgs {
     const uint8_t* M;
     const BlockDev* blocks;
@@ -244,10 +333,59 @@ struct GemvArgs {
     const float* out_scale;
     float* out;
     long long out_stride;
+    FinaliseArgs fin;
 };
 
-template <int DT, int U, int RPW>
+#ifndef RTC_GEMV_F32_U
+#define RTC_GEMV_F32_U 4
+#endif
+#ifndef RTC_GEMV_F32_RI
+#define RTC_GEMV_F32_RI 1
+#endif
+#ifndef RTC_GEMV_BF16_U
+#define RTC_GEMV_BF16_U 4
+#endif
+#ifndef RTC_GEMV_BF16_RI
+#define RTC_GEMV_BF16_RI 2
+#endif
+#ifndef RTC_GEMV_E4M3_U
+#define RTC_GEMV_E4M3_U 2
+#endif
+#ifndef RTC_GEMV_E4M3_RI
+#define RTC_GEMV_E4M3_RI 4
+#endif
+
+// The master's finalisation of one tile of kFinRows rows (Section 3: sum the
+// partial commands; Section 3.4: add the implicit-POLC term; leaky integrator).
+// Eight thread groups each add a contiguous range of blocks in block order,
+// then the eight group sums are added in group order.
+__device__ void finalise_tile(const FinaliseArgs& f, const float* __restrict__ partial, int na, int ft) {
+    __shared__ float red[kGemvWarps][32];
+    const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
+    const int r = ft * kFinRows + lane;
+    const int b0 = (seg * f.nblk) / kGemvWarps, b1 = ((seg + 1) * f.nblk) / kGemvWarps;
+    float y = 0.f;
+    if (r < na)
+        for (int b = b0; b < b1; ++b) y += __ldcg(partial + (size_t)b * na + r);
+    red[seg][lane] = y;
+    __syncthreads();
+    if (seg == 0 && r < na) {
+        float t = 0.f;
+#pragma unroll
+        for (int k = 0; k < kGemvWarps; ++k) t += red[k][lane];
+        if (f.scale) t *= f.scale[r];
+        const float w = t + f.q[r];
+        float v = fmaf(f.gain, w, f.oml * f.a[r]);
+        if (f.clip) v = fminf(fmaxf(v, f.amin), f.amax);
+        f.a[r] = v;
+        f.cmd[r] = v;
+    }
+}
+
+template <int DT, int U, int RI, int RPW>
 __global__ void __launch_bounds__(kGemvWarps * 32) gemv_kernel(const __grid_constant__ GemvArgs a) {
+    static_assert(RPW % RI == 0 && kFinRows % (kGemvWarps * RPW) == 0, "row tiling");
+    __shared__ int s_last;
     const int bi = blockIdx.x / a.tiles;
     const int tile = blockIdx.x - bi * a.tiles;
     const int b = a.b0 + bi;
@@ -255,82 +393,93 @@ __global__ void __launch_bounds__(kGemvWarps * 32) gemv_kernel(const __grid_cons
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nvec = B.pitch / Elem<DT>::kPer16;
     const float* x = a.x + B.x_off;
-    const size_t esz = 16 / Elem<DT>::kPer16;
-    const int rbase = (tile * kGemvWarps + warp) * RPW;
+    constexpr size_t esz = 16 / Elem<DT>::kPer16;
+    const int r0 = tile * kGemvWarps * RPW;
+    const int rbase = r0 + warp * RPW;
 #pragma unroll 1
-    for (int rr = 0; rr < RPW; ++rr) {
-        const int r = rbase + rr;
-        if (r >= a.na) break;
-        const uint4* mrow = reinterpret_cast<const uint4*>(a.M + (size_t)(B.m_off + (long long)r * B.pitch) * esz);
-        float acc = 0.f;
+    for (int rr = 0; rr < RPW; rr += RI) {
+        const uint4* mrow[RI];
+        bool ok[RI];
+        float acc[RI];
+#pragma unroll
+        for (int i = 0; i < RI; ++i) {
+            const int r = rbase + rr + i;
+            ok[i] = r < a.na;
+            mrow[i] = reinterpret_cast<const uint4*>(a.M + (size_t)(B.m_off + (long long)(ok[i] ? r : 0) * B.pitch) * esz);
+            acc[i] = 0.f;
+        }
 #pragma unroll 1
         for (int v0 = lane; v0 < nvec; v0 += 32 * U) {
-            uint4 m[U];
+            uint4 m[RI][U];
+#pragma unroll
+            for (int i = 0; i < RI; ++i)
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int v = v0 + 32 * u;
+                    m[i][u] = (ok[i] && v < nvec) ? ld_stream(mrow[i] + v) : make_uint4(0u, 0u, 0u, 0u);
+                }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int v = v0 + 32 * u;
-                m[u] = v < nvec ? ld_stream(mrow + v) : make_uint4(0u, 0u, 0u, 0u);
-            }
+                if (v < nvec) {
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int v = v0 + 32 * u;
-                if (v < nvec) acc = dot16<DT>(m[u], x, v, acc);
+                    for (int i = 0; i < RI; ++i) acc[i] = dot16<DT>(m[i][u], x, v, acc[i]);
+                }
             }
         }
-        acc = warp_sum(acc);
-        if (lane == 0) {
-            if (a.out_scale) acc *= a.out_scale[r];
-            a.out[(long long)b * a.out_stride + r] = acc;
+#pragma unroll
+        for (int i = 0; i < RI; ++i) {
+            const float t = warp_sum(acc[i]);
+            const int r = rbase + rr + i;
+            if (lane == 0 && ok[i]) a.out[(long long)b * a.out_stride + r] = a.out_scale ? t * a.out_scale[r] : t;
         }
     }
+    if (!a.fin.enabled) return;
+    // Fused finalisation: the CTA that completes the last block of a row tile
+    // (counted in rows, across launches of the same frame) finalises it.
+    __threadfence();
+    __syncthreads();
+    const int ft = r0 / kFinRows;
+    if (threadIdx.x == 0) {
+        const int rows_here = min(r0 + kGemvWarps * RPW, a.na) - r0;
+        const int ft_rows = min(kFinRows, a.na - ft * kFinRows);
+        const unsigned prev = atomicAdd(&a.fin.counters[ft], (unsigned)rows_here);
+        s_last = prev + rows_here == (unsigned)(a.fin.nblk * ft_rows);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    finalise_tile(a.fin, a.out, a.na, ft);
+    if (threadIdx.x == 0) a.fin.counters[ft] = 0u;
 }
 
-cudaError_t launch_gemv(int dtype, const void* M, const BlockDev* blocks, int b0, int nb, int na,
-                        const float* x, const float* out_scale, float* out, long long out_stride,
+template <int DT, int U, int RI>
+cudaError_t launch_gemv_t(const GemvArgs& base, int nb, cudaStream_t st) {
+    // rows per warp: as many as keep at least 8 CTAs per SM in flight
+    const int na = base.na;
+    int rpw = 4;
+    while (rpw > RI && (long long)((na + kGemvWarps * rpw - 1) / (kGemvWarps * rpw)) * nb < 8LL * 152) rpw /= 2;
+    GemvArgs a = base;
+    a.tiles = (na + kGemvWarps * rpw - 1) / (kGemvWarps * rpw);
+    const dim3 grid((unsigned)(a.tiles * nb));
+    if (rpw >= 4) gemv_kernel<DT, U, RI, (RI > 4 ? RI : 4)><<<grid, kGemvWarps * 32, 0, st>>>(a);
+    else if (rpw >= 2) gemv_kernel<DT, U, RI, (RI > 2 ? RI : 2)><<<grid, kGemvWarps * 32, 0, st>>>(a);
+    else gemv_kernel<DT, U, RI, RI><<<grid, kGemvWarps * 32, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemv(int dtype, const void* M, const BlockDev* blocks, int b0, int nb, int na, const float* x,
+                        const float* out_scale, float* out, long long out_stride, const FinaliseArgs* fin,
                         cudaStream_t st) {
     if (nb <= 0 || na <= 0) return cudaSuccess;
-    constexpr int U = 4, RPW = 4;
-    const int rows_per_cta = kGemvWarps * RPW;
-    const int tiles = (na + rows_per_cta - 1) / rows_per_cta;
-    GemvArgs a{static_cast<const uint8_t*>(M), blocks, b0, tiles, na, x, out_scale, out, out_stride};
-    const dim3 grid(tiles * nb);
+    GemvArgs a{static_cast<const uint8_t*>(M), blocks, b0, 0, na, x, out_scale, out, out_stride, FinaliseArgs{}};
+    if (fin) a.fin = *fin;
     switch (dtype) {
-        case RTC_F32: gemv_kernel<RTC_F32, U, RPW><<<grid, kGemvWarps * 32, 0, st>>>(a); break;
-        case RTC_BF16: gemv_kernel<RTC_BF16, U, RPW><<<grid, kGemvWarps * 32, 0, st>>>(a); break;
-        case RTC_E4M3: gemv_kernel<RTC_E4M3, U, RPW><<<grid, kGemvWarps * 32, 0, st>>>(a); break;
+        case RTC_F32: return launch_gemv_t<RTC_F32, RTC_GEMV_F32_U, RTC_GEMV_F32_RI>(a, nb, st);
+        case RTC_BF16: return launch_gemv_t<RTC_BF16, RTC_GEMV_BF16_U, RTC_GEMV_BF16_RI>(a, nb, st);
+        case RTC_E4M3: return launch_gemv_t<RTC_E4M3, RTC_GEMV_E4M3_U, RTC_GEMV_E4M3_RI>(a, nb, st);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// Finalise: the master's sum of partial commands (Section 3) in block order,
-// the row scale of a quantised matrix, the implicit-POLC term q = P a_{k-1}
-// (Section 3.4) and the leaky integrator.  Commands go to device state and to
-// the page-locked ring (mapped host memory).
-// ---------------------------------------------------------------------------
-__global__ void finalise_kernel(const float* __restrict__ partial, int nblk, int na,
-                                const float* __restrict__ scale, const float* __restrict__ q,
-                                float* __restrict__ a, float* __restrict__ cmd, float oml, float gain,
-                                int clip, float amin, float amax) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= na) return;
-    float y = 0.f;
-    for (int b = 0; b < nblk; ++b) y += partial[(size_t)b * na + r];
-    if (scale) y *= scale[r];
-    const float w = y + q[r];
-    float v = fmaf(gain, w, oml * a[r]);
-    if (clip) v = fminf(fmaxf(v, amin), amax);
-    a[r] = v;
-    cmd[r] = v;
-}
-
-cudaError_t launch_finalise(const float* partial, int nblk, int na, const float* scale, const float* q,
-                            float* a, float* cmd, float oml, float gain, int clip, float amin, float amax,
-                            cudaStream_t st) {
-    finalise_kernel<<<(na + 255) / 256, 256, 0, st>>>(partial, nblk, na, scale, q, a, cmd, oml, gain, clip,
-                                                       amin, amax);
-    return cudaGetLastError();
 }
 
 __global__ void pack_slopes_kernel(const BlockDev* __restrict__ blocks, const float* __restrict__ s_pad,

@@ -46,6 +46,7 @@ struct rtc_loop {
     std::vector<rtc_wfs> wfs;
     std::vector<int> wfs_row0, wfs_nrows, wfs_blk0, wfs_nblk;
     std::vector<int> row_ready;     // per table row: pixel rows of its WFS needed
+    std::vector<int> part_start;    // per table row (+1): first slope-kernel part of the row
     std::vector<int> blk_row_end;   // per block: end (exclusive) of its slope rows within the WFS
     std::vector<BlockDev> blocks_h;
     int max_cols = 0, smem_bytes = 0;
@@ -61,6 +62,11 @@ struct rtc_loop {
     std::vector<float*> d_dark, d_flat;
     WfsDev* d_wfs = nullptr;
     SlopeRow* d_rows = nullptr;
+    SlopePart* d_parts = nullptr;
+    float* d_pscr = nullptr;                // per-part subaperture sums of split rows
+    unsigned* d_row_cnt = nullptr;          // per slope row: parts finished
+    unsigned* d_fin_cnt = nullptr;          // per finalisation tile: rows finished over blocks
+    int nfin = 0;
     uint16_t* d_xlist = nullptr;
     float* d_ref = nullptr;
     std::vector<uint16_t*> d_frame;
@@ -356,6 +362,34 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
         }
     L->nrows = (int)rows.size();
     L->nblk = (int)L->blocks_h.size();
+    // Slope-kernel parts: an SH subaperture row is split by pixel rows so that no
+    // thread of its CTA loads more than four rows of one quad column.
+    std::vector<SlopePart> parts;
+    size_t pscr_floats = 0;
+    for (int r = 0; r < L->nrows; ++r) {
+        SlopeRow& R = rows[r];
+        const rtc_wfs& w = L->wfs[R.wfs];
+        int np = 1;
+        if (w.kind == RTC_WFS_SH) {
+            const int nq = ((w.ox + w.nsubx * w.npx + 3) >> 2) - (w.ox >> 2);
+            const int gfull = std::max(1, kSlopeThreads / nq);
+            np = std::min(w.npx, std::max(1, (w.npx + 4 * gfull - 1) / (4 * gfull)));
+        }
+        R.nparts = np;
+        R.pscr = (int)pscr_floats;
+        if (np > 1) pscr_floats += (size_t)np * R.nunits * 3;
+        L->part_start.push_back((int)parts.size());
+        for (int k = 0; k < np; ++k) {
+            SlopePart P{};
+            P.row = r;
+            P.part = k;
+            P.pr0 = w.kind == RTC_WFS_SH ? (k * w.npx) / np : 0;
+            P.pr1 = w.kind == RTC_WFS_SH ? ((k + 1) * w.npx) / np : 0;
+            parts.push_back(P);
+        }
+    }
+    L->part_start.push_back((int)parts.size());
+    L->nfin = (L->na + kFinRows - 1) / kFinRows;
     L->ns = compact;
     if (M->ns != L->ns)
         return fail(L, RTC_EINVAL, "cmat ns = " + std::to_string(M->ns) + " but the geometry has " +
@@ -454,6 +488,13 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
     CK(L, cudaMemcpy(L->d_wfs, wdev.data(), wdev.size() * sizeof(WfsDev), cudaMemcpyHostToDevice));
     TRY(dev_alloc(L, &L->d_rows, rows.size() * sizeof(SlopeRow)));
     CK(L, cudaMemcpy(L->d_rows, rows.data(), rows.size() * sizeof(SlopeRow), cudaMemcpyHostToDevice));
+    TRY(dev_alloc(L, &L->d_parts, parts.size() * sizeof(SlopePart)));
+    CK(L, cudaMemcpy(L->d_parts, parts.data(), parts.size() * sizeof(SlopePart), cudaMemcpyHostToDevice));
+    TRY(dev_alloc(L, &L->d_pscr, std::max<size_t>(pscr_floats, 4) * 4));
+    TRY(dev_alloc(L, &L->d_row_cnt, (size_t)L->nrows * sizeof(unsigned)));
+    CK(L, cudaMemset(L->d_row_cnt, 0, (size_t)L->nrows * sizeof(unsigned)));
+    TRY(dev_alloc(L, &L->d_fin_cnt, (size_t)L->nfin * sizeof(unsigned)));
+    CK(L, cudaMemset(L->d_fin_cnt, 0, (size_t)L->nfin * sizeof(unsigned)));
     TRY(dev_alloc(L, &L->d_xlist, std::max<size_t>(xlist.size(), 1) * 2));
     if (!xlist.empty()) CK(L, cudaMemcpy(L->d_xlist, xlist.data(), xlist.size() * 2, cudaMemcpyHostToDevice));
     if (C && C->ref_slopes) {
@@ -470,7 +511,7 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
     TRY(dev_alloc(L, &L->d_q, (size_t)L->na * 4));
     CK(L, cudaMemset(L->d_q, 0, (size_t)L->na * 4));
     if (L->has_polc) {
-        CK(L, launch_gemv(L->p_dtype, L->d_P, L->d_pblock, 0, 1, L->na, L->d_a, L->d_Pscale, L->d_q, 0, L->st));
+        CK(L, launch_gemv(L->p_dtype, L->d_P, L->d_pblock, 0, 1, L->na, L->d_a, L->d_Pscale, L->d_q, 0, nullptr, L->st));
     }
 
     // ---- page-locked ring, events -------------------------------------------
@@ -535,9 +576,7 @@ void begin_frame(rtc_loop* L, uint64_t id, bool chunked) {
 int finish_frame(rtc_loop* L) {
     Slot& s = L->slots[L->cur_slot];
     float* cmd = L->d_ring + (size_t)L->cur_slot * L->slot_floats;
-    CK(L, launch_finalise(L->d_part, L->nblk, L->na, L->d_Mscale, L->d_q, L->d_a, cmd, 1.0f - L->leak, L->gain,
-                          L->clip, L->amin, L->amax, L->st));
-    CK(L, cudaEventRecord(s.ev_final, L->st));
+    CK(L, cudaEventRecord(s.ev_final, L->st));   // the last MVM launch finalised every row tile
     if (L->telemetry) {
         CK(L, cudaStreamWaitEvent(L->st_tel, s.ev_final, 0));
         CK(L, launch_pack_slopes(L->d_blocks, L->nblk, std::max(L->max_cols, 1), L->d_s,
@@ -547,7 +586,7 @@ int finish_frame(rtc_loop* L) {
         CK(L, cudaEventRecord(s.ev_tel, L->st));
     }
     if (L->has_polc)
-        CK(L, launch_gemv(L->p_dtype, L->d_P, L->d_pblock, 0, 1, L->na, L->d_a, L->d_Pscale, L->d_q, 0, L->st));
+        CK(L, launch_gemv(L->p_dtype, L->d_P, L->d_pblock, 0, 1, L->na, L->d_a, L->d_Pscale, L->d_q, 0, nullptr, L->st));
     if (L->timing) CK(L, cudaEventRecord(s.ev_polc, L->st));
     if (L->telemetry) CK(L, cudaStreamWaitEvent(L->st, s.ev_tel, 0));   // the next frame rewrites the slopes
     {
@@ -561,6 +600,36 @@ int finish_frame(rtc_loop* L) {
     L->have_last = true;
     L->last_id = L->cur_id;
     ++L->seq;
+    return RTC_OK;
+}
+
+FinaliseArgs fin_args(rtc_loop* L) {
+    FinaliseArgs f{};
+    f.enabled = 1;
+    f.nblk = L->nblk;
+    f.counters = L->d_fin_cnt;
+    f.scale = L->d_Mscale;
+    f.q = L->d_q;
+    f.a = L->d_a;
+    f.cmd = L->d_ring + (size_t)L->cur_slot * L->slot_floats;
+    f.oml = 1.0f - L->leak;
+    f.gain = L->gain;
+    f.clip = L->clip;
+    f.amin = L->amin;
+    f.amax = L->amax;
+    return f;
+}
+
+int slopes_rows(rtc_loop* L, int r0, int r1, const FramePtrs& fp) {
+    const int p0 = L->part_start[r0], p1 = L->part_start[r1];
+    CK(L, launch_slopes(L->d_parts, p0, p1 - p0, L->d_rows, L->d_wfs, fp, L->d_xlist, L->d_ref, L->d_s, L->d_pscr,
+                        L->d_row_cnt, L->smem_bytes, L->st));
+    return RTC_OK;
+}
+
+// A dropped frame may have counted some blocks of some row tiles: clear them.
+int reset_counters(rtc_loop* L) {
+    CK(L, cudaMemsetAsync(L->d_fin_cnt, 0, (size_t)L->nfin * sizeof(unsigned), L->st));
     return RTC_OK;
 }
 
@@ -586,6 +655,7 @@ int submit_impl(rtc_loop* L, const rtc_chunk* c) {
         if (c->row_begin != 0) return fail(L, RTC_EORDER, "new frame must start at row 0");
         ++L->frames_dropped;
         L->active = false;
+        TRY(reset_counters(L));
         status = RTC_EDROPPED;
         L->err = "frame " + std::to_string(L->cur_id) + " was incomplete and has been dropped";
     }
@@ -615,8 +685,7 @@ int submit_impl(rtc_loop* L, const rtc_chunk* c) {
     int upto = done;
     while (upto < L->wfs_nrows[k] && L->row_ready[r0 + upto] <= L->rows_in[k]) ++upto;
     if (upto > done) {
-        CK(L, launch_slopes(L->d_rows, r0 + done, upto - done, L->d_wfs, internal_frames(L), L->d_xlist, L->d_ref,
-                            L->d_s, L->smem_bytes, L->st));
+        TRY(slopes_rows(L, r0 + done, r0 + upto, internal_frames(L)));
         L->rows_done[k] = upto;
     }
     if (last && L->timing) CK(L, cudaEventRecord(s.ev_slopes, L->st));
@@ -626,8 +695,9 @@ int submit_impl(rtc_loop* L, const rtc_chunk* c) {
     int bu = bd;
     while (bu < L->wfs_nblk[k] && L->blk_row_end[b0 + bu] <= L->rows_done[k]) ++bu;
     if (bu > bd) {
+        const FinaliseArgs fa = fin_args(L);
         CK(L, launch_gemv(L->m_dtype, L->d_M, L->d_blocks, b0 + bd, bu - bd, L->na, L->d_s, nullptr, L->d_part, L->na,
-                          L->st));
+                          &fa, L->st));
         L->blks_done[k] = bu;
     }
     if (last) {
@@ -660,6 +730,7 @@ int process_impl(rtc_loop* L, uint64_t id, const uint16_t* const* px, const size
     if (L->active) {
         ++L->frames_dropped;
         L->active = false;
+        TRY(reset_counters(L));
         status = RTC_EDROPPED;
         L->err = "frame " + std::to_string(L->cur_id) + " was incomplete and has been dropped";
     }
@@ -669,9 +740,11 @@ int process_impl(rtc_loop* L, uint64_t id, const uint16_t* const* px, const size
         CK(L, cudaEventRecord(s.ev_start, L->st));
         CK(L, cudaEventRecord(s.ev_tail, L->st));
     }
-    CK(L, launch_slopes(L->d_rows, 0, L->nrows, L->d_wfs, fp, L->d_xlist, L->d_ref, L->d_s, L->smem_bytes, L->st));
+    TRY(slopes_rows(L, 0, L->nrows, fp));
     if (L->timing) CK(L, cudaEventRecord(s.ev_slopes, L->st));
-    CK(L, launch_gemv(L->m_dtype, L->d_M, L->d_blocks, 0, L->nblk, L->na, L->d_s, nullptr, L->d_part, L->na, L->st));
+    const FinaliseArgs fa = fin_args(L);
+    CK(L, launch_gemv(L->m_dtype, L->d_M, L->d_blocks, 0, L->nblk, L->na, L->d_s, nullptr, L->d_part, L->na, &fa,
+                      L->st));
     if (L->timing) CK(L, cudaEventRecord(s.ev_mvm, L->st));
     TRY(finish_frame(L));
     return status;
@@ -826,7 +899,7 @@ int rtc_set_state(rtc_loop* L, const float* a, size_t na) {
     CK(L, cudaStreamSynchronize(L->st));
     CK(L, cudaMemcpy(L->d_a, a, na * 4, cudaMemcpyHostToDevice));
     if (L->has_polc)
-        CK(L, launch_gemv(L->p_dtype, L->d_P, L->d_pblock, 0, 1, L->na, L->d_a, L->d_Pscale, L->d_q, 0, L->st));
+        CK(L, launch_gemv(L->p_dtype, L->d_P, L->d_pblock, 0, 1, L->na, L->d_a, L->d_Pscale, L->d_q, 0, nullptr, L->st));
     CK(L, cudaStreamSynchronize(L->st));
     return RTC_OK;
 }
