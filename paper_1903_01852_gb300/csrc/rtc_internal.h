@@ -63,10 +63,12 @@ struct FinaliseArgs {
     float amin, amax;
 };
 
-// Frame pointers for one launch; pitch in uint16 elements.
+// Frame pointers for one launch; pitch in uint16 elements.  px[w] holds pixel
+// row row0[w] of WFS w (row0 > 0 when only a chunk of the frame is addressed).
 struct FramePtrs {
     const uint16_t* px[kMaxWfs];
     long long pitch[kMaxWfs];
+    int row0[kMaxWfs];
 };
 
 // One reconstruction column block, stored as a dense [na][pitch] sub-matrix.

@@ -45,7 +45,7 @@ __device__ __forceinline__ float calibrate(unsigned raw, float dark, float flat,
 // subapertures) publishes per-part sums; the last part to finish adds them in
 // part order and writes the slopes.  Every sum has a fixed order.
 __device__ void sh_part(const SlopePart& P, const SlopeRow& row, const WfsDev& W, const uint16_t* __restrict__ px,
-                        long long pitch, const uint16_t* __restrict__ xlist, const float* __restrict__ ref,
+                        long long pitch, int prow0, const uint16_t* __restrict__ xlist, const float* __restrict__ ref,
                         float* __restrict__ s_pad, float* __restrict__ pscr, unsigned* __restrict__ counters,
                         float* sm) {
     __shared__ int s_last;
@@ -76,7 +76,7 @@ __device__ void sh_part(const SlopePart& P, const SlopeRow& row, const WfsDev& W
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const long long yy = y0 + r + k * G;
-                rw[k] = __ldg(reinterpret_cast<const uint2*>(px + yy * pitch + xa));
+                rw[k] = __ldg(reinterpret_cast<const uint2*>(px + (yy - prow0) * pitch + xa));
                 d[k] = __ldg(reinterpret_cast<const float4*>(W.dark + yy * W.calib_pitch + xa));
                 f[k] = __ldg(reinterpret_cast<const float4*>(W.flat + yy * W.calib_pitch + xa));
             }
@@ -94,7 +94,7 @@ __device__ void sh_part(const SlopePart& P, const SlopeRow& row, const WfsDev& W
         }
         for (; r < P.pr1; r += G) {
             const long long yy = y0 + r;
-            const uint2 rw = __ldg(reinterpret_cast<const uint2*>(px + yy * pitch + xa));
+            const uint2 rw = __ldg(reinterpret_cast<const uint2*>(px + (yy - prow0) * pitch + xa));
             const float4 d = __ldg(reinterpret_cast<const float4*>(W.dark + yy * W.calib_pitch + xa));
             const float4 f = __ldg(reinterpret_cast<const float4*>(W.flat + yy * W.calib_pitch + xa));
             const float yc = float(r) - half;
@@ -187,7 +187,7 @@ __device__ void sh_part(const SlopePart& P, const SlopeRow& row, const WfsDev& W
 // of the four pupil images A (top-left), B (top-right), C (bottom-left),
 // D (bottom-right); sx = (A+C-B-D)/N, sy = (A+B-C-D)/N with N = A+B+C+D.
 __device__ void pyr_row(const SlopeRow& row, const WfsDev& W, const uint16_t* __restrict__ px,
-                        long long pitch, const uint16_t* __restrict__ xlist,
+                        long long pitch, int prow0, const uint16_t* __restrict__ xlist,
                         const float* __restrict__ ref, float* __restrict__ s_pad) {
     const int i = row.row;
     for (int u = threadIdx.x; u < row.nunits; u += blockDim.x) {
@@ -197,7 +197,7 @@ __device__ void pyr_row(const SlopeRow& row, const WfsDev& W, const uint16_t* __
         for (int k = 0; k < 4; ++k) {
             const int yy = W.qy[k] + i, xx = W.qx[k] + j;
             const size_t m = (size_t)yy * W.calib_pitch + xx;
-            v[k] = calibrate(px[yy * pitch + xx], __ldg(W.dark + m), __ldg(W.flat + m), W.threshold,
+            v[k] = calibrate(px[(long long)(yy - prow0) * pitch + xx], __ldg(W.dark + m), __ldg(W.flat + m), W.threshold,
                              W.thresh_mode);
         }
         const float N = (v[0] + v[1]) + (v[2] + v[3]);
@@ -231,9 +231,10 @@ __global__ void __launch_bounds__(kSlopeThreads) slopes_kernel(const __grid_cons
     const SlopeRow row = a.rows[P.row];
     const WfsDev W = a.wfs[row.wfs];
     if (W.kind == RTC_WFS_SH)
-        sh_part(P, row, W, a.fp.px[row.wfs], a.fp.pitch[row.wfs], a.xlist, a.ref, a.s_pad, a.pscr, a.counters, sm);
+        sh_part(P, row, W, a.fp.px[row.wfs], a.fp.pitch[row.wfs], a.fp.row0[row.wfs], a.xlist, a.ref, a.s_pad, a.pscr,
+                a.counters, sm);
     else
-        pyr_row(row, W, a.fp.px[row.wfs], a.fp.pitch[row.wfs], a.xlist, a.ref, a.s_pad);
+        pyr_row(row, W, a.fp.px[row.wfs], a.fp.pitch[row.wfs], a.fp.row0[row.wfs], a.xlist, a.ref, a.s_pad);
 }
 
 cudaError_t configure_slopes(int smem_bytes) {

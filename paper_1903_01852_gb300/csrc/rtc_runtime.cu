@@ -633,6 +633,20 @@ int reset_counters(rtc_loop* L) {
     return RTC_OK;
 }
 
+// Device address through which kernels can read p in place: device or managed
+// memory, or page-locked host memory (read over the CPU-GPU link); NULL for
+// pageable memory, which must be copied.
+const void* device_view(const void* p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged || at.type == cudaMemoryTypeHost)
+        return at.devicePointer;
+    return nullptr;
+}
+
 FramePtrs internal_frames(rtc_loop* L) {
     FramePtrs fp{};
     for (int k = 0; k < L->nwfs; ++k) {
@@ -676,16 +690,36 @@ int submit_impl(rtc_loop* L, const rtc_chunk* c) {
         if (got < L->wfs[j].height) last = false;
     }
     if (last && L->timing) CK(L, cudaEventRecord(s.ev_tail, L->st));
-    CK(L, cudaMemcpy2DAsync(L->d_frame[k] + (size_t)c->row_begin * L->frame_pitch[k], L->frame_pitch[k] * 2, c->px,
-                            c->pitch, (size_t)w.width * 2, c->row_end - c->row_begin, cudaMemcpyDefault, L->st));
-    L->rows_in[k] = c->row_end;
     // slope rows completed by these rows
     const int r0 = L->wfs_row0[k];
-    int done = L->rows_done[k];
+    const int done = L->rows_done[k];
     int upto = done;
-    while (upto < L->wfs_nrows[k] && L->row_ready[r0 + upto] <= L->rows_in[k]) ++upto;
+    while (upto < L->wfs_nrows[k] && L->row_ready[r0 + upto] <= c->row_end) ++upto;
+    // Read the chunk in place when it is device-accessible, aligned, and holds
+    // exactly whole subaperture rows: every row those slope rows need, and no
+    // row a later chunk's subaperture row would need.  Otherwise copy it into
+    // the loop's frame buffer.
+    FramePtrs fp = internal_frames(L);
+    bool in_place = false;
+    if (w.kind == RTC_WFS_SH && (c->pitch & 15u) == 0 && (reinterpret_cast<uintptr_t>(c->px) & 15u) == 0 &&
+        c->pitch >= round_up((size_t)w.width * 2, 16)) {
+        const bool needed_here = upto == done || w.oy + done * w.npx >= c->row_begin;
+        const bool no_leftover = upto >= w.nsuby || c->row_end <= w.oy + upto * w.npx;
+        if (needed_here && no_leftover) {
+            if (const void* dv = device_view(c->px)) {
+                in_place = true;
+                fp.px[k] = static_cast<const uint16_t*>(dv);
+                fp.pitch[k] = (long long)(c->pitch / 2);
+                fp.row0[k] = c->row_begin;
+            }
+        }
+    }
+    if (!in_place)
+        CK(L, cudaMemcpy2DAsync(L->d_frame[k] + (size_t)c->row_begin * L->frame_pitch[k], L->frame_pitch[k] * 2, c->px,
+                                c->pitch, (size_t)w.width * 2, c->row_end - c->row_begin, cudaMemcpyDefault, L->st));
+    L->rows_in[k] = c->row_end;
     if (upto > done) {
-        TRY(slopes_rows(L, r0 + done, r0 + upto, internal_frames(L)));
+        TRY(slopes_rows(L, r0 + done, r0 + upto, fp));
         L->rows_done[k] = upto;
     }
     if (last && L->timing) CK(L, cudaEventRecord(s.ev_slopes, L->st));
@@ -715,14 +749,11 @@ int process_impl(rtc_loop* L, uint64_t id, const uint16_t* const* px, const size
         if (!px[k] || (reinterpret_cast<uintptr_t>(px[k]) & 15u) || (pitch[k] & 15u) ||
             pitch[k] < round_up((size_t)w.width * 2, 16))
             return fail(L, RTC_EINVAL, "frame " + std::to_string(k) + ": pointer/pitch not 16-byte aligned or too small");
-        cudaPointerAttributes at{};
-        if (cudaPointerGetAttributes(&at, px[k]) != cudaSuccess ||
-            (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
-            cudaGetLastError();
-            return fail(L, RTC_EINVAL, "frame " + std::to_string(k) + " is not device memory");
-        }
-        fp.px[k] = px[k];
+        const void* dv = device_view(px[k]);
+        if (!dv) return fail(L, RTC_EINVAL, "frame " + std::to_string(k) + " is neither device nor page-locked memory");
+        fp.px[k] = static_cast<const uint16_t*>(dv);
         fp.pitch[k] = (long long)(pitch[k] / 2);
+        fp.row0[k] = 0;
     }
     int status = RTC_OK;
     if (L->active ? id <= L->cur_id : (L->have_last && id <= L->last_id))

@@ -291,3 +291,53 @@ def test_full_size_mcao_bf16_against_stored_and_true_matrix(rtc, torch_cuda, mca
     true_err = [rel(a, ref.step(f)[1]) for f, a in zip(frames, cmds)]
     print("mcao bf16 errors vs stored matrix:", errs, "vs float32 matrix:", true_err)
     assert max(true_err) < 2.0 ** -8 * 8
+
+
+def test_chunks_read_in_place_or_copied_give_identical_commands(rtc, torch_cuda):
+    # Device-resident chunks whose boundaries fall on subaperture rows are read in
+    # place; the others are copied.  Every mixture must give the same bits.
+    torch = torch_cuda
+    cfg = synth.make_config("scao_small", nblocks=4)
+    frames = synth.draw_frames(cfg, 3, seed=95)
+    dev = [device_frames(f)[0] for f in frames]
+    host_pinned = []
+    for f in frames:
+        t = torch.empty((128, 128), dtype=torch.int16, pin_memory=True)
+        t.numpy()[:] = f[0].view(np.int16)
+        host_pinned.append(t)
+    plans = {
+        "aligned": synth.chunk_plan(cfg["wfs"][0], 4),
+        "ragged": [(0, 13), (13, 40), (40, 41), (41, 96), (96, 128)],
+        "mixed": [(0, 16), (16, 37), (37, 64), (64, 128)],
+    }
+    results = {}
+    for name, plan in plans.items():
+        for src_name, src in (("device", dev), ("pinned", host_pinned), ("pageable", [f[0] for f in frames])):
+            with rtc.Loop(cfg, telemetry=True) as loop:
+                out = []
+                for k, f in enumerate(src):
+                    for r0, r1 in plan:
+                        loop.submit(k + 1, 0, r0, r1, f[r0:r1])
+                    out.append(loop.get_commands(timeout_us=WAIT_US)[1])
+            results[(name, src_name)] = out
+    ref = results[("ragged", "pageable")]
+    for key, out in results.items():
+        assert all(np.array_equal(a, b) for a, b in zip(out, ref)), key
+    ora = OracleLoop(cfg)
+    for f, a in zip(frames, ref):
+        assert rel(a, ora.step(f)[1]) <= TOL_F32
+
+
+def test_process_frame_from_page_locked_host_memory(rtc, torch_cuda):
+    torch = torch_cuda
+    cfg = synth.make_config("scao_small")
+    frames = synth.draw_frames(cfg, 3, seed=96)
+    with rtc.Loop(cfg, telemetry=True) as a, rtc.Loop(cfg, telemetry=True) as b:
+        for k, f in enumerate(frames):
+            t = torch.empty((128, 128), dtype=torch.int16, pin_memory=True)
+            t.numpy()[:] = f[0].view(np.int16)
+            a.process_frame(k + 1, [t])
+            b.process_frame(k + 1, device_frames(f))
+            ca = a.get_commands(timeout_us=WAIT_US)[1]
+            cb = b.get_commands(timeout_us=WAIT_US)[1]
+            assert np.array_equal(ca, cb)
