@@ -155,16 +155,23 @@ def make_workload(seed_frames=1, name="mcao"):
     return cfg, frames
 
 
-def bf16_config(cfg, rtc, torch):
+def quant_config(cfg, rtc, torch, fmt):
+    """The same loop with M and P stored as per-row scaled BF16 / E4M3 codes
+    (quantised on the GPU by rtc_quantize_rows)."""
     import copy
     q = copy.copy(cfg)
-    codes, scale = rtc.quantize_rows(torch.from_numpy(cfg["M"]).cuda(), "bf16")
-    pc, ps = rtc.quantize_rows(torch.from_numpy(cfg["P"]).cuda(), "bf16")
+    view = np.uint16 if fmt == "bf16" else np.uint8
+    codes, scale = rtc.quantize_rows(torch.from_numpy(cfg["M"]).cuda(), fmt)
+    q.update(M=codes.cpu().numpy().view(view), M_scale=scale.cpu().numpy(), M_dtype=fmt)
+    if cfg.get("P") is not None:
+        pc, ps = rtc.quantize_rows(torch.from_numpy(cfg["P"]).cuda(), fmt)
+        q.update(P=pc.cpu().numpy().view(view), P_scale=ps.cpu().numpy(), P_dtype=fmt)
     torch.cuda.synchronize()
-    q.update(M=codes.cpu().numpy().view(np.uint16), M_scale=scale.cpu().numpy(), M_dtype="bf16",
-             P=pc.cpu().numpy().view(np.uint16), P_scale=ps.cpu().numpy(), P_dtype="bf16")
-    del codes, pc
     return q
+
+
+def bf16_config(cfg, rtc, torch):
+    return quant_config(cfg, rtc, torch, "bf16")
 
 
 def mvm_bytes(info, cfg):
@@ -363,6 +370,8 @@ def ours_arm(args, world, rank, local):
     peak, peak_kind = peaks()
     cfg, frames = make_workload(name=args.workload)
     if args.quick:
+        if args.dtype != "f32":
+            cfg = quant_config(cfg, rtc, torch, args.dtype)
         return quick_arm(args, cfg, frames, rtc, torch, local)
     dev_frames = []
     for f in frames:
@@ -389,18 +398,22 @@ def ours_arm(args, world, rank, local):
     out = {}
     loops = {}
     try:
-        loops["f32"] = rtc.Loop(cfg, device=local, timing=True, telemetry=True)
         bcfg = bf16_config(cfg, rtc, torch)
-        loops["bf16"] = rtc.Loop(bcfg, device=local, timing=True, telemetry=True)
         cfgs = {"f32": cfg, "bf16": bcfg}
+        for name in ("f32", "bf16"):
+            # latency loops: the MVM starts while the slope kernel runs (frame-level events only)
+            loops[name] = rtc.Loop(cfgs[name], device=local, timing=True, telemetry=True)
+            # stage loops: slope and MVM kernels timed separately (serialised) for the MVM bandwidth
+            loops[name + "_stage"] = rtc.Loop(cfgs[name], device=local, stage_timing=True, telemetry=True)
         fid = 1
         # 1) timed region: K unpaced steps, frames resident in HBM (device events around the region)
         ms_total, ids, _, fid = run_unpaced(loops["f32"], dev_frames, args.steps, args.warmup, torch, sampler, fid)
-        # per-frame stage times, FP32 and BF16
-        per = {}
+        # per-frame latencies and per-kernel stage times, FP32 and BF16
+        per, stg = {}, {}
         for name in ("f32", "bf16"):
-            rows, fid = run_unpaced_timed(loops[name], dev_frames, args.steps, args.warmup, sampler, fid)
-            per[name] = rows
+            per[name], fid = run_unpaced_timed(loops[name], dev_frames, args.steps, args.warmup, sampler, fid)
+            stg[name], fid = run_unpaced_timed(loops[name + "_stage"], dev_frames, args.steps, args.warmup, sampler,
+                                               fid)
         # 2) end-to-end through the C ABI from page-locked host buffers (unpaced, whole frames)
         e2e_lat, fid = run_host_frames(loops["f32"], host_frames, args.steps, args.warmup, sampler, fid)
         # 3) camera-paced last-pixel latency (the paper's definition), FP32 and BF16
@@ -413,10 +426,10 @@ def ours_arm(args, world, rank, local):
     finally:
         sampler.stop()
     lat = {n: stats([r["latency_us"] for r in per[n]]) for n in per}
-    mvm_us = {n: statistics.median([r["mvm_us"] for r in per[n]]) for n in per}
-    gbs = {n: mvm_bytes(infos[n], cfgs[n]) / (mvm_us[n] * 1e-6) / 1e9 for n in per}
-    stage = {n: {k: statistics.median([r[k] for r in per[n]]) for k in ("slopes_us", "mvm_us", "final_us", "polc_us")}
-             for n in per}
+    mvm_us = {n: statistics.median([r["mvm_us"] for r in stg[n]]) for n in stg}
+    gbs = {n: mvm_bytes(infos[n], cfgs[n]) / (mvm_us[n] * 1e-6) / 1e9 for n in stg}
+    stage = {n: {k: statistics.median([r[k] for r in stg[n]]) for k in ("slopes_us", "mvm_us", "polc_us")}
+             for n in stg}
 
     # CPU oracle on the host cores (rank 0, N=1 only), plus parity of the first frames
     cpu = None
@@ -473,7 +486,7 @@ def ours_arm(args, world, rank, local):
         "roofline": {"bound": "hbm", "achieved": gbs["f32"], "peak": peak, "unit": "GB/s",
                      "frac": gbs["f32"] / peak, "traffic": traffic, "kernel": "gemv_kernel<f32> (reconstruction MVM)",
                      "algorithmic_bytes_per_launch": mb, "peak_kind": peak_kind},
-        "gpu_launches": 5 * args.steps,
+        "gpu_launches": 4 * args.steps,   # per frame: slopes, MVM (with finalisation), telemetry pack, POLC
         "clocks": sampler.summary(),
     }
     if cpu:
@@ -497,10 +510,15 @@ def quick_arm(args, cfg, frames, rtc, torch, local):
     sampler = ClockSampler(local)
     with rtc.Loop(cfg, device=local, timing=True, telemetry=True) as loop:
         rows, _ = run_unpaced_timed(loop, dev_frames, args.steps, args.warmup, sampler, 1)
+    with rtc.Loop(cfg, device=local, stage_timing=True, telemetry=True) as loop:
+        srows, _ = run_unpaced_timed(loop, dev_frames, args.steps, args.warmup, sampler, 1)
         info = loop.info()
     lat = stats([r["latency_us"] for r in rows])
-    mvm = statistics.median([r["mvm_us"] for r in rows])
-    print(json.dumps({"workload": args.workload, "quick": True, "latency_us": lat, "mvm_us": mvm,
+    mvm = statistics.median([r["mvm_us"] for r in srows])
+    sl = statistics.median([r["slopes_us"] for r in srows])
+    po = statistics.median([r["polc_us"] for r in srows])
+    print(json.dumps({"workload": args.workload, "quick": True, "dtype": args.dtype, "latency_us": lat,
+                      "slopes_us": sl, "polc_us": po, "mvm_us": mvm,
                       "mvm_gbs": mvm_bytes(info, cfg) / (mvm * 1e-6) / 1e9}), flush=True)
 
 
@@ -512,7 +530,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--workload", default="mcao", help="configuration (profiling aid; the bench line is mcao)")
-    ap.add_argument("--quick", action="store_true", help="profiling aid: only the unpaced float32 loop")
+    ap.add_argument("--quick", action="store_true", help="profiling aid: only the unpaced loop")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "e4m3"], help="matrix storage for --quick")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -63,8 +63,10 @@ extern "C" {
 #define RTC_THRESH_SUBTRACT 0  /* t = max(c - T, 0) */
 #define RTC_THRESH_CLIP     1  /* t = c if c > T else 0 */
 
-#define RTC_FLAG_TIMING     1u /* record per-stage CUDA events (rtc_get_timing) */
+#define RTC_FLAG_TIMING     1u /* record frame-level CUDA events (rtc_get_timing) */
 #define RTC_FLAG_TELEMETRY  2u /* copy slopes of every frame to the page-locked ring */
+#define RTC_FLAG_STAGE_TIMING 4u /* also time the slope and MVM kernels separately; this
+                                    serialises them (no early start of the MVM) */
 
 #define RTC_MAX_WFS 16
 
@@ -217,11 +219,14 @@ int rtc_get_commands(rtc_loop* loop, float* out, size_t n, uint64_t* frame_id,
 int rtc_get_telemetry(rtc_loop* loop, uint64_t frame_id, float* slopes, size_t ns,
                       float* cmds, size_t na, int64_t timeout_us);
 
-/* Device times of one frame's stages, from CUDA events on the loop's stream
- * (needs RTC_FLAG_TIMING).  For rtc_process_frame: slopes, MVM, finalise
- * and POLC kernels, and latency = start of the slope kernel to the end of
- * the finalise kernel.  For chunked frames: stage times of the last chunk,
- * and latency = start of the last chunk's copy to the end of finalise. */
+/* Device times of one frame, from CUDA events on the loop's stream (needs
+ * RTC_FLAG_TIMING).  latency_us: for rtc_process_frame, from just before the
+ * slope kernel to the end of the MVM kernel, whose tail writes the commands;
+ * for chunked frames, from just before the last chunk's work.  frame_us: from
+ * the frame's first submitted work to the commands.  polc_us: the POLC
+ * product after the commands.  slopes_us and mvm_us (the MVM kernel with its
+ * fused finalisation) need RTC_FLAG_STAGE_TIMING, else they are -1;
+ * final_us is 0 (the finalisation is part of the MVM kernel). */
 typedef struct rtc_timing {
     uint64_t frame_id;
     float slopes_us, mvm_us, final_us, polc_us;

@@ -14,14 +14,15 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "librtc.so")
+# RTC_LIBRARY may name another build of the same library (e.g. one compiled with other tuning macros).
+LIB_PATH = os.environ.get("RTC_LIBRARY") or os.path.join(HERE, "librtc.so")
 
 RTC_OK, RTC_EINVAL, RTC_ENOMEM, RTC_ETIMEDOUT = 0, -1, -2, -3
 RTC_EORDER, RTC_EDROPPED, RTC_ECUDA, RTC_ENOENT = -4, -5, -6, -7
 RTC_WFS_SH, RTC_WFS_PYRAMID = 0, 1
 RTC_F32, RTC_BF16, RTC_E4M3 = 0, 1, 2
 RTC_THRESH_SUBTRACT, RTC_THRESH_CLIP = 0, 1
-RTC_FLAG_TIMING, RTC_FLAG_TELEMETRY = 1, 2
+RTC_FLAG_TIMING, RTC_FLAG_TELEMETRY, RTC_FLAG_STAGE_TIMING = 1, 2, 4
 RTC_MAX_WFS = 16
 DTYPES = {"f32": RTC_F32, "bf16": RTC_BF16, "e4m3": RTC_E4M3}
 CODE_NP = {RTC_F32: np.float32, RTC_BF16: np.uint16, RTC_E4M3: np.uint8}
@@ -156,7 +157,7 @@ def _pitch(x):
 class Loop:
     """One AO loop on one GPU, built from a configuration dict (see synth)."""
 
-    def __init__(self, cfg, device=0, timing=False, telemetry=False, ring=4):
+    def __init__(self, cfg, device=0, timing=False, telemetry=False, ring=4, stage_timing=False):
         self.cfg = cfg
         self.na = int(cfg["na"])
         wl = cfg["wfs"]
@@ -187,7 +188,8 @@ class Loop:
             keep += [d, f]
             darks[k] = _fptr(d)
             flats[k] = _fptr(f)
-        flags = (RTC_FLAG_TIMING if timing else 0) | (RTC_FLAG_TELEMETRY if telemetry else 0)
+        flags = ((RTC_FLAG_TIMING if timing or stage_timing else 0) | (RTC_FLAG_TELEMETRY if telemetry else 0)
+                 | (RTC_FLAG_STAGE_TIMING if stage_timing else 0))
         geo = rtc_geometry(len(wl), warr, device, flags, ring)
         ref = _f32(cfg.get("ref_slopes"))
         cal = rtc_calib(darks, flats, thr.ctypes.data_as(f32p), mode.ctypes.data_as(C.POINTER(C.c_int32)), _fptr(ref))

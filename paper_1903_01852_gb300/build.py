@@ -35,20 +35,25 @@ def _stale(target, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, ptxas_verbose: bool = False, quiet: bool = True) -> str:
-    os.makedirs(OBJ, exist_ok=True)
+def build(force: bool = False, ptxas_verbose: bool = False, quiet: bool = True, defines=(), out=None) -> str:
+    """Compile and link the library; ``defines`` adds -D tuning macros and ``out``
+    names another output path (objects then go next to it)."""
+    obj_dir = OBJ if out is None else os.path.join(os.path.dirname(os.path.abspath(out)), "_build")
+    lib = LIB if out is None else os.path.abspath(out)
+    os.makedirs(obj_dir, exist_ok=True)
     cc = nvcc()
     common = ["-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC,-O2",
               "-I", os.path.join(ROOT, "include")]
     if ptxas_verbose:
         common += ["-Xptxas", "-v"]
+    common += [f"-D{d}" for d in defines]
     procs = []
     objs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(OBJ, src.replace(".cu", ".o"))
+        o = os.path.join(obj_dir, src.replace(".cu", ".o"))
         objs.append(o)
-        if force or ptxas_verbose or _stale(o, [s, *HEADERS]):
+        if force or ptxas_verbose or defines or _stale(o, [s, *HEADERS]):
             cmd = [cc, *common, "-c", s, "-o", o]
             procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     for cmd, p in procs:
@@ -58,14 +63,14 @@ def build(force: bool = False, ptxas_verbose: bool = False, quiet: bool = True) 
             raise RuntimeError("nvcc failed: " + " ".join(cmd) + "\n" + text)
         if text.strip() and (ptxas_verbose or not quiet):
             sys.stdout.write(text)
-    if force or procs or _stale(LIB, objs):
-        tmp = LIB + ".tmp"
+    if force or procs or _stale(lib, objs):
+        tmp = lib + ".tmp"
         cmd = [cc, "-shared", *ARCH, "-o", tmp, *objs]
         r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
         if r.returncode != 0:
             raise RuntimeError("link failed: " + " ".join(cmd) + "\n" + r.stdout.decode(errors="replace"))
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

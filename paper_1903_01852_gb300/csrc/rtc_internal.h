@@ -61,6 +61,9 @@ struct FinaliseArgs {
     float oml, gain;          // 1 - leak, gain
     int clip;
     float amin, amax;
+    unsigned* tiles_done;     // tiles finalised this frame
+    unsigned long long* done_flag;  // page-locked completion word of the ring slot, or NULL
+    unsigned long long seq;   // value written to done_flag once every tile is final
 };
 
 // Frame pointers for one launch; pitch in uint16 elements.  px[w] holds pixel
@@ -94,10 +97,14 @@ cudaError_t launch_slopes(const SlopePart* parts, int part0, int nparts, const S
 
 // GEMV over blocks [b0, b0 + nb): out[b * out_stride + r] = sum_j M_b[r][j] x[x_off_b + j],
 // times out_scale[r] when out_scale is not NULL; with fin, the CTA completing the
-// last block of a row tile also finalises it (a, cmd).
+// last block of a row tile also finalises it (a, cmd) and the last tile sets the
+// completion word.  pdl: launched as a programmatic dependent of the previous
+// kernel in the stream (prefetches matrix tiles into L2, then waits for it);
+// avg_row_bytes sizes that prefetch.
 cudaError_t launch_gemv(int dtype, const void* M, const BlockDev* blocks, int b0, int nb,
                         int na, const float* x, const float* out_scale, float* out,
-                        long long out_stride, const FinaliseArgs* fin, cudaStream_t st);
+                        long long out_stride, const FinaliseArgs* fin, long long avg_row_bytes,
+                        bool pdl, cudaStream_t st);
 
 // Telemetry: compact copy of the padded slope buffer, block by block.
 cudaError_t launch_pack_slopes(const BlockDev* blocks, int nblk, int max_cols,

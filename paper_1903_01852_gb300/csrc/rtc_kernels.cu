@@ -9,6 +9,8 @@
 //                    sums + POLC term + leaky integrator, Section 3 and 3.4)
 //                    fused into its tail; also the POLC product P a
 //   pack / relayout / quantize / check kernels used at creation and for telemetry
+#include <algorithm>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -24,6 +26,17 @@ __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// Programmatic dependent launch: a kernel lets the next one in its stream start
+// early (launch_dependents); the next one waits (wait) before it reads anything
+// the previous one writes.  Both are no-ops without the launch attribute.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Bulk prefetch of a contiguous, 16-byte aligned region into L2 (TMA engine).
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -227,6 +240,7 @@ struct SlopeArgs {
 
 __global__ void __launch_bounds__(kSlopeThreads) slopes_kernel(const __grid_constant__ SlopeArgs a) {
     extern __shared__ float sm[];
+    pdl_trigger();        // the MVM may launch now and prefetch its matrix tiles while slopes run
     const SlopePart P = a.parts[a.part0 + blockIdx.x];
     const SlopeRow row = a.rows[P.row];
     const WfsDev W = a.wfs[row.wfs];
@@ -335,6 +349,7 @@ struct GemvArgs {
     float* out;
     long long out_stride;
     FinaliseArgs fin;
+    int prefetch_ctas;         // CTAs [0, prefetch_ctas) prefetch their matrix tile into L2 before waiting
 };
 
 #ifndef RTC_GEMV_F32_U
@@ -344,13 +359,13 @@ struct GemvArgs {
 #define RTC_GEMV_F32_RI 1
 #endif
 #ifndef RTC_GEMV_BF16_U
-#define RTC_GEMV_BF16_U 4
+#define RTC_GEMV_BF16_U 2
 #endif
 #ifndef RTC_GEMV_BF16_RI
-#define RTC_GEMV_BF16_RI 2
+#define RTC_GEMV_BF16_RI 4
 #endif
 #ifndef RTC_GEMV_E4M3_U
-#define RTC_GEMV_E4M3_U 2
+#define RTC_GEMV_E4M3_U 1
 #endif
 #ifndef RTC_GEMV_E4M3_RI
 #define RTC_GEMV_E4M3_RI 4
@@ -397,6 +412,13 @@ __global__ void __launch_bounds__(kGemvWarps * 32) gemv_kernel(const __grid_cons
     constexpr size_t esz = 16 / Elem<DT>::kPer16;
     const int r0 = tile * kGemvWarps * RPW;
     const int rbase = r0 + warp * RPW;
+    if (threadIdx.x == 0 && (int)blockIdx.x < a.prefetch_ctas && r0 < a.na) {
+        const int rows = min(r0 + kGemvWarps * RPW, a.na) - r0;
+        const unsigned bytes = (unsigned)((size_t)rows * B.pitch * esz);
+        if (bytes) prefetch_l2(a.M + (size_t)(B.m_off + (long long)r0 * B.pitch) * esz, bytes);
+    }
+    pdl_wait();           // the input vector (slopes or commands) is written by the previous kernel
+    pdl_trigger();
 #pragma unroll 1
     for (int rr = 0; rr < RPW; rr += RI) {
         const uint4* mrow[RI];
@@ -451,11 +473,39 @@ __global__ void __launch_bounds__(kGemvWarps * 32) gemv_kernel(const __grid_cons
     if (!s_last) return;
     __threadfence();
     finalise_tile(a.fin, a.out, a.na, ft);
-    if (threadIdx.x == 0) a.fin.counters[ft] = 0u;
+    // commands of this tile visible to the host before the tile counts as done
+    __threadfence_system();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a.fin.counters[ft] = 0u;
+        if (a.fin.done_flag) {
+            const int nfin = (a.na + kFinRows - 1) / kFinRows;
+            if (atomicAdd(a.fin.tiles_done, 1u) == (unsigned)(nfin - 1)) {
+                *a.fin.tiles_done = 0u;
+                __threadfence_system();
+                *reinterpret_cast<volatile unsigned long long*>(a.fin.done_flag) = a.fin.seq;
+            }
+        }
+    }
+}
+
+template <typename K>
+cudaError_t launch_maybe_pdl(K kernel, dim3 grid, const GemvArgs& a, bool pdl, cudaStream_t st) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(kGemvWarps * 32);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, a);
 }
 
 template <int DT, int U, int RI>
-cudaError_t launch_gemv_t(const GemvArgs& base, int nb, cudaStream_t st) {
+cudaError_t launch_gemv_t(const GemvArgs& base, int nb, long long avg_row_bytes, bool pdl, cudaStream_t st) {
     // rows per warp: as many as keep at least 8 CTAs per SM in flight
     const int na = base.na;
     int rpw = 4;
@@ -463,22 +513,24 @@ cudaError_t launch_gemv_t(const GemvArgs& base, int nb, cudaStream_t st) {
     GemvArgs a = base;
     a.tiles = (na + kGemvWarps * rpw - 1) / (kGemvWarps * rpw);
     const dim3 grid((unsigned)(a.tiles * nb));
-    if (rpw >= 4) gemv_kernel<DT, U, RI, (RI > 4 ? RI : 4)><<<grid, kGemvWarps * 32, 0, st>>>(a);
-    else if (rpw >= 2) gemv_kernel<DT, U, RI, (RI > 2 ? RI : 2)><<<grid, kGemvWarps * 32, 0, st>>>(a);
-    else gemv_kernel<DT, U, RI, RI><<<grid, kGemvWarps * 32, 0, st>>>(a);
-    return cudaGetLastError();
+    // prefetch while waiting for the producer: about 96 MB, below the L2 size
+    const long long tile_bytes = std::max(1LL, avg_row_bytes * kGemvWarps * rpw);
+    a.prefetch_ctas = pdl ? (int)std::min<long long>(grid.x, (96LL << 20) / tile_bytes) : 0;
+    if (rpw >= 4) return launch_maybe_pdl(gemv_kernel<DT, U, RI, (RI > 4 ? RI : 4)>, grid, a, pdl, st);
+    if (rpw >= 2) return launch_maybe_pdl(gemv_kernel<DT, U, RI, (RI > 2 ? RI : 2)>, grid, a, pdl, st);
+    return launch_maybe_pdl(gemv_kernel<DT, U, RI, RI>, grid, a, pdl, st);
 }
 
 cudaError_t launch_gemv(int dtype, const void* M, const BlockDev* blocks, int b0, int nb, int na, const float* x,
                         const float* out_scale, float* out, long long out_stride, const FinaliseArgs* fin,
-                        cudaStream_t st) {
+                        long long avg_row_bytes, bool pdl, cudaStream_t st) {
     if (nb <= 0 || na <= 0) return cudaSuccess;
-    GemvArgs a{static_cast<const uint8_t*>(M), blocks, b0, 0, na, x, out_scale, out, out_stride, FinaliseArgs{}};
+    GemvArgs a{static_cast<const uint8_t*>(M), blocks, b0, 0, na, x, out_scale, out, out_stride, FinaliseArgs{}, 0};
     if (fin) a.fin = *fin;
     switch (dtype) {
-        case RTC_F32: return launch_gemv_t<RTC_F32, RTC_GEMV_F32_U, RTC_GEMV_F32_RI>(a, nb, st);
-        case RTC_BF16: return launch_gemv_t<RTC_BF16, RTC_GEMV_BF16_U, RTC_GEMV_BF16_RI>(a, nb, st);
-        case RTC_E4M3: return launch_gemv_t<RTC_E4M3, RTC_GEMV_E4M3_U, RTC_GEMV_E4M3_RI>(a, nb, st);
+        case RTC_F32: return launch_gemv_t<RTC_F32, RTC_GEMV_F32_U, RTC_GEMV_F32_RI>(a, nb, avg_row_bytes, pdl, st);
+        case RTC_BF16: return launch_gemv_t<RTC_BF16, RTC_GEMV_BF16_U, RTC_GEMV_BF16_RI>(a, nb, avg_row_bytes, pdl, st);
+        case RTC_E4M3: return launch_gemv_t<RTC_E4M3, RTC_GEMV_E4M3_U, RTC_GEMV_E4M3_RI>(a, nb, avg_row_bytes, pdl, st);
         default: return cudaErrorInvalidValue;
     }
 }

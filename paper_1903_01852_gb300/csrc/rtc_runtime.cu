@@ -1,6 +1,7 @@
 // Host runtime of the AO RTC library: loop objects, plans, streams, events,
 // the page-locked command ring and the C ABI declared in include/rtc.h.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -15,6 +16,10 @@
 
 using namespace rtc;
 
+#ifndef RTC_SLOPE_ROWS_PER_THREAD
+#define RTC_SLOPE_ROWS_PER_THREAD 12
+#endif
+
 namespace {
 
 thread_local std::string g_err;
@@ -25,6 +30,7 @@ size_t round_up(size_t x, size_t m) { return (x + m - 1) / m * m; }
 
 struct Slot {
     uint64_t frame_id = 0;
+    uint64_t seq = 0;         // value of the slot's completion word once its commands are written
     bool used = false;        // holds a frame whose submission completed
     bool chunked = false;
     cudaEvent_t ev_start = nullptr, ev_tail = nullptr, ev_slopes = nullptr, ev_mvm = nullptr;
@@ -40,7 +46,7 @@ struct rtc_loop {
     int m_dtype = RTC_F32, p_dtype = RTC_F32;
     float gain = 0.f, leak = 0.f, amin = 0.f, amax = 0.f;
     int clip = 0;
-    bool has_polc = false, timing = false, telemetry = false;
+    bool has_polc = false, timing = false, telemetry = false, stage_timing = false;
 
     // host plans
     std::vector<rtc_wfs> wfs;
@@ -80,6 +86,10 @@ struct rtc_loop {
     // page-locked ring: per slot na commands then ns slopes
     float* h_ring = nullptr;
     float* d_ring = nullptr;
+    unsigned long long* h_done = nullptr;   // page-locked completion words, one per slot
+    unsigned long long* d_done = nullptr;
+    unsigned* d_tiles_done = nullptr;
+    uint64_t frame_seq = 0;
     size_t slot_floats = 0;
     std::vector<Slot> slots;
 
@@ -175,6 +185,7 @@ void release(rtc_loop* L) {
             if (e) cudaEventDestroy(e);
     for (void* p : L->allocs) cudaFree(p);
     if (L->h_ring) cudaFreeHost(L->h_ring);
+    if (L->h_done) cudaFreeHost(L->h_done);
     if (L->st) cudaStreamDestroy(L->st);
     if (L->st_tel) cudaStreamDestroy(L->st_tel);
     cudaGetLastError();
@@ -253,7 +264,8 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
 
     L->dev = G->device;
     L->flags = G->flags;
-    L->timing = (G->flags & RTC_FLAG_TIMING) != 0;
+    L->stage_timing = (G->flags & RTC_FLAG_STAGE_TIMING) != 0;
+    L->timing = (G->flags & RTC_FLAG_TIMING) != 0 || L->stage_timing;
     L->telemetry = (G->flags & RTC_FLAG_TELEMETRY) != 0;
     L->ring = G->ring > 0 ? G->ring : 4;
     if (L->ring < 2 || L->ring > 1024) return fail(L, RTC_EINVAL, "ring must be in [2, 1024]");
@@ -363,7 +375,7 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
     L->nrows = (int)rows.size();
     L->nblk = (int)L->blocks_h.size();
     // Slope-kernel parts: an SH subaperture row is split by pixel rows so that no
-    // thread of its CTA loads more than four rows of one quad column.
+    // thread of its CTA loads more than RTC_SLOPE_ROWS_PER_THREAD rows of one quad column.
     std::vector<SlopePart> parts;
     size_t pscr_floats = 0;
     for (int r = 0; r < L->nrows; ++r) {
@@ -373,7 +385,8 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
         if (w.kind == RTC_WFS_SH) {
             const int nq = ((w.ox + w.nsubx * w.npx + 3) >> 2) - (w.ox >> 2);
             const int gfull = std::max(1, kSlopeThreads / nq);
-            np = std::min(w.npx, std::max(1, (w.npx + 4 * gfull - 1) / (4 * gfull)));
+            const int rpt = RTC_SLOPE_ROWS_PER_THREAD;
+            np = std::min(w.npx, std::max(1, (w.npx + rpt * gfull - 1) / (rpt * gfull)));
         }
         R.nparts = np;
         R.pscr = (int)pscr_floats;
@@ -511,7 +524,7 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
     TRY(dev_alloc(L, &L->d_q, (size_t)L->na * 4));
     CK(L, cudaMemset(L->d_q, 0, (size_t)L->na * 4));
     if (L->has_polc) {
-        CK(L, launch_gemv(L->p_dtype, L->d_P, L->d_pblock, 0, 1, L->na, L->d_a, L->d_Pscale, L->d_q, 0, nullptr, L->st));
+        CK(L, launch_gemv(L->p_dtype, L->d_P, L->d_pblock, 0, 1, L->na, L->d_a, L->d_Pscale, L->d_q, 0, nullptr, 0, false, L->st));
     }
 
     // ---- page-locked ring, events -------------------------------------------
@@ -529,17 +542,32 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
         CK(L, cudaHostGetDevicePointer(&d, h, 0));
         L->d_ring = static_cast<float*>(d);
     }
+    {
+        void* h = nullptr;
+        cudaError_t e = cudaHostAlloc(&h, (size_t)L->ring * sizeof(unsigned long long), cudaHostAllocMapped);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(L, RTC_ENOMEM, "page-locked completion words");
+        }
+        L->h_done = static_cast<unsigned long long*>(h);
+        std::memset(h, 0, (size_t)L->ring * sizeof(unsigned long long));
+        void* d = nullptr;
+        CK(L, cudaHostGetDevicePointer(&d, h, 0));
+        L->d_done = static_cast<unsigned long long*>(d);
+    }
+    TRY(dev_alloc(L, &L->d_tiles_done, sizeof(unsigned)));
+    CK(L, cudaMemset(L->d_tiles_done, 0, sizeof(unsigned)));
     L->slots.resize(L->ring);
     const unsigned evflags = L->timing ? cudaEventDefault : cudaEventDisableTiming;
     for (auto& s : L->slots) {
-        CK(L, cudaEventCreateWithFlags(&s.ev_final, evflags));
+        CK(L, cudaEventCreateWithFlags(&s.ev_polc, evflags));
         CK(L, cudaEventCreateWithFlags(&s.ev_tel, cudaEventDisableTiming));
         if (L->timing) {
             CK(L, cudaEventCreate(&s.ev_start));
             CK(L, cudaEventCreate(&s.ev_tail));
+            CK(L, cudaEventCreate(&s.ev_final));
             CK(L, cudaEventCreate(&s.ev_slopes));
             CK(L, cudaEventCreate(&s.ev_mvm));
-            CK(L, cudaEventCreate(&s.ev_polc));
         }
     }
     L->rows_in.assign(L->nwfs, 0);
@@ -565,6 +593,7 @@ void begin_frame(rtc_loop* L, uint64_t id, bool chunked) {
         s.used = false;
         s.frame_id = id;
         s.chunked = chunked;
+        s.seq = ++L->frame_seq;
     }
     std::fill(L->rows_in.begin(), L->rows_in.end(), 0);
     std::fill(L->rows_done.begin(), L->rows_done.end(), 0);
@@ -572,23 +601,25 @@ void begin_frame(rtc_loop* L, uint64_t id, bool chunked) {
     L->tail_recorded = false;
 }
 
-// Finalise, POLC for the next frame, telemetry, then publish the slot.
+// After the MVM (whose tail wrote the commands): POLC for the next frame,
+// telemetry, then publish the slot.
 int finish_frame(rtc_loop* L) {
     Slot& s = L->slots[L->cur_slot];
     float* cmd = L->d_ring + (size_t)L->cur_slot * L->slot_floats;
-    CK(L, cudaEventRecord(s.ev_final, L->st));   // the last MVM launch finalised every row tile
+    if (L->timing) CK(L, cudaEventRecord(s.ev_final, L->st));
+    if (L->has_polc)
+        CK(L, launch_gemv(L->p_dtype, L->d_P, L->d_pblock, 0, 1, L->na, L->d_a, L->d_Pscale, L->d_q, 0, nullptr,
+                          (long long)(L->p_bytes / std::max(L->na, 1)), !L->timing, L->st));
+    CK(L, cudaEventRecord(s.ev_polc, L->st));
     if (L->telemetry) {
-        CK(L, cudaStreamWaitEvent(L->st_tel, s.ev_final, 0));
+        CK(L, cudaStreamWaitEvent(L->st_tel, s.ev_polc, 0));
         CK(L, launch_pack_slopes(L->d_blocks, L->nblk, std::max(L->max_cols, 1), L->d_s,
                                  cmd + round_up((size_t)L->na, 4), L->st_tel));
         CK(L, cudaEventRecord(s.ev_tel, L->st_tel));
+        CK(L, cudaStreamWaitEvent(L->st, s.ev_tel, 0));   // the next frame rewrites the slopes
     } else {
         CK(L, cudaEventRecord(s.ev_tel, L->st));
     }
-    if (L->has_polc)
-        CK(L, launch_gemv(L->p_dtype, L->d_P, L->d_pblock, 0, 1, L->na, L->d_a, L->d_Pscale, L->d_q, 0, nullptr, L->st));
-    if (L->timing) CK(L, cudaEventRecord(s.ev_polc, L->st));
-    if (L->telemetry) CK(L, cudaStreamWaitEvent(L->st, s.ev_tel, 0));   // the next frame rewrites the slopes
     {
         std::lock_guard<std::mutex> g(L->mu);
         s.used = true;
@@ -617,6 +648,9 @@ FinaliseArgs fin_args(rtc_loop* L) {
     f.clip = L->clip;
     f.amin = L->amin;
     f.amax = L->amax;
+    f.tiles_done = L->d_tiles_done;
+    f.done_flag = L->d_done + L->cur_slot;
+    f.seq = L->slots[L->cur_slot].seq;
     return f;
 }
 
@@ -625,6 +659,10 @@ int slopes_rows(rtc_loop* L, int r0, int r1, const FramePtrs& fp) {
     CK(L, launch_slopes(L->d_parts, p0, p1 - p0, L->d_rows, L->d_wfs, fp, L->d_xlist, L->d_ref, L->d_s, L->d_pscr,
                         L->d_row_cnt, L->smem_bytes, L->st));
     return RTC_OK;
+}
+
+long long avg_row_bytes(const rtc_loop* L) {
+    return (long long)(L->m_bytes / ((uint64_t)std::max(L->na, 1) * std::max(L->nblk, 1)));
 }
 
 // A dropped frame may have counted some blocks of some row tiles: clear them.
@@ -718,11 +756,12 @@ int submit_impl(rtc_loop* L, const rtc_chunk* c) {
         CK(L, cudaMemcpy2DAsync(L->d_frame[k] + (size_t)c->row_begin * L->frame_pitch[k], L->frame_pitch[k] * 2, c->px,
                                 c->pitch, (size_t)w.width * 2, c->row_end - c->row_begin, cudaMemcpyDefault, L->st));
     L->rows_in[k] = c->row_end;
-    if (upto > done) {
+    const bool slopes_launched = upto > done;
+    if (slopes_launched) {
         TRY(slopes_rows(L, r0 + done, r0 + upto, fp));
         L->rows_done[k] = upto;
     }
-    if (last && L->timing) CK(L, cudaEventRecord(s.ev_slopes, L->st));
+    if (last && L->stage_timing) CK(L, cudaEventRecord(s.ev_slopes, L->st));
     // column blocks completed by those slope rows
     const int b0 = L->wfs_blk0[k];
     int bd = L->blks_done[k];
@@ -731,11 +770,11 @@ int submit_impl(rtc_loop* L, const rtc_chunk* c) {
     if (bu > bd) {
         const FinaliseArgs fa = fin_args(L);
         CK(L, launch_gemv(L->m_dtype, L->d_M, L->d_blocks, b0 + bd, bu - bd, L->na, L->d_s, nullptr, L->d_part, L->na,
-                          &fa, L->st));
+                          &fa, avg_row_bytes(L), slopes_launched && !L->stage_timing, L->st));
         L->blks_done[k] = bu;
     }
     if (last) {
-        if (L->timing) CK(L, cudaEventRecord(s.ev_mvm, L->st));
+        if (L->stage_timing) CK(L, cudaEventRecord(s.ev_mvm, L->st));
         TRY(finish_frame(L));
     }
     return status;
@@ -772,11 +811,11 @@ int process_impl(rtc_loop* L, uint64_t id, const uint16_t* const* px, const size
         CK(L, cudaEventRecord(s.ev_tail, L->st));
     }
     TRY(slopes_rows(L, 0, L->nrows, fp));
-    if (L->timing) CK(L, cudaEventRecord(s.ev_slopes, L->st));
+    if (L->stage_timing) CK(L, cudaEventRecord(s.ev_slopes, L->st));
     const FinaliseArgs fa = fin_args(L);
     CK(L, launch_gemv(L->m_dtype, L->d_M, L->d_blocks, 0, L->nblk, L->na, L->d_s, nullptr, L->d_part, L->na, &fa,
-                      L->st));
-    if (L->timing) CK(L, cudaEventRecord(s.ev_mvm, L->st));
+                      avg_row_bytes(L), !L->stage_timing, L->st));
+    if (L->stage_timing) CK(L, cudaEventRecord(s.ev_mvm, L->st));
     TRY(finish_frame(L));
     return status;
 }
@@ -788,6 +827,24 @@ int wait_event(rtc_loop* L, cudaEvent_t ev, Clock::time_point deadline, bool for
         if (e == cudaSuccess) return RTC_OK;
         if (e != cudaErrorNotReady) return cuda_fail(L, e, "cudaEventQuery");
         if (!forever && Clock::now() >= deadline) return fail(L, RTC_ETIMEDOUT, "timed out waiting for the GPU");
+    }
+}
+
+// Busy-poll the slot's page-locked completion word until it holds the frame's
+// sequence number or the deadline passes; every few thousand polls also ask the
+// stream whether a kernel failed.
+int wait_done(rtc_loop* L, int slot, uint64_t seq, Clock::time_point deadline, bool forever) {
+    const volatile unsigned long long* w = L->h_done + slot;
+    for (unsigned n = 1;; ++n) {
+        if (*w == seq) {
+            std::atomic_thread_fence(std::memory_order_acquire);
+            return RTC_OK;
+        }
+        if ((n & 4095u) == 0) {
+            const cudaError_t e = cudaStreamQuery(L->st);
+            if (e != cudaSuccess && e != cudaErrorNotReady) return cuda_fail(L, e, "kernel failed");
+            if (!forever && Clock::now() >= deadline) return fail(L, RTC_ETIMEDOUT, "timed out waiting for the GPU");
+        }
     }
 }
 
@@ -867,7 +924,12 @@ int rtc_get_commands(rtc_loop* L, float* out, size_t n, uint64_t* frame_id, int6
             }
             slot = L->pending.front();
         }
-        TRY(wait_event(L, L->slots[slot].ev_final, deadline, forever));
+        uint64_t seq;
+        {
+            std::lock_guard<std::mutex> g(L->mu);
+            seq = L->slots[slot].seq;
+        }
+        TRY(wait_done(L, slot, seq, deadline, forever));
         std::lock_guard<std::mutex> g(L->mu);
         if (L->pending.empty() || L->pending.front() != slot) continue;   // discarded meanwhile
         L->pending.pop_front();
@@ -886,7 +948,6 @@ int rtc_get_telemetry(rtc_loop* L, uint64_t frame_id, float* slopes, size_t ns, 
     const int slot = find_slot(L, frame_id);
     if (slot < 0) return fail(L, RTC_ENOENT, "frame not in the ring");
     const auto deadline = deadline_of(timeout_us);
-    TRY(wait_event(L, L->slots[slot].ev_final, deadline, timeout_us < 0));
     TRY(wait_event(L, L->slots[slot].ev_tel, deadline, timeout_us < 0));
     std::lock_guard<std::mutex> g(L->mu);
     if (!L->slots[slot].used || L->slots[slot].frame_id != frame_id) return fail(L, RTC_ENOENT, "frame left the ring");
@@ -906,9 +967,9 @@ int rtc_get_timing(rtc_loop* L, uint64_t frame_id, rtc_timing* out, int64_t time
     const auto deadline = deadline_of(timeout_us);
     TRY(wait_event(L, s.ev_polc, deadline, timeout_us < 0));
     out->frame_id = frame_id;
-    out->slopes_us = elapsed(s.ev_tail, s.ev_slopes);
-    out->mvm_us = elapsed(s.ev_slopes, s.ev_mvm);
-    out->final_us = elapsed(s.ev_mvm, s.ev_final);
+    out->slopes_us = L->stage_timing ? elapsed(s.ev_tail, s.ev_slopes) : -1.f;
+    out->mvm_us = L->stage_timing ? elapsed(s.ev_slopes, s.ev_mvm) : -1.f;
+    out->final_us = 0.f;
     out->polc_us = elapsed(s.ev_final, s.ev_polc);
     out->latency_us = elapsed(s.ev_tail, s.ev_final);
     out->frame_us = elapsed(s.ev_start, s.ev_final);
@@ -930,7 +991,7 @@ int rtc_set_state(rtc_loop* L, const float* a, size_t na) {
     CK(L, cudaStreamSynchronize(L->st));
     CK(L, cudaMemcpy(L->d_a, a, na * 4, cudaMemcpyHostToDevice));
     if (L->has_polc)
-        CK(L, launch_gemv(L->p_dtype, L->d_P, L->d_pblock, 0, 1, L->na, L->d_a, L->d_Pscale, L->d_q, 0, nullptr, L->st));
+        CK(L, launch_gemv(L->p_dtype, L->d_P, L->d_pblock, 0, 1, L->na, L->d_a, L->d_Pscale, L->d_q, 0, nullptr, 0, false, L->st));
     CK(L, cudaStreamSynchronize(L->st));
     return RTC_OK;
 }

@@ -341,3 +341,26 @@ def test_process_frame_from_page_locked_host_memory(rtc, torch_cuda):
             ca = a.get_commands(timeout_us=WAIT_US)[1]
             cb = b.get_commands(timeout_us=WAIT_US)[1]
             assert np.array_equal(ca, cb)
+
+
+@pytest.mark.parametrize("mode", ["device", "chunked"])
+def test_overlapped_and_serialised_launches_give_identical_commands(rtc, torch_cuda, mode):
+    # Without stage timing the MVM (and the POLC product) start before their
+    # producer kernel finishes and wait for it on the device; with it they run
+    # strictly after.  Same bits either way, and the frame timing is sane.
+    cfg = synth.make_config("elt_scao_sh", polc=True, with_ref=True)
+    frames = synth.draw_frames(cfg, 3, seed=97)
+    out = {}
+    for name, kw in (("overlap", dict(timing=True)), ("serial", dict(stage_timing=True)), ("plain", {})):
+        with rtc.Loop(cfg, telemetry=True, **kw) as loop:
+            errs, cmds = run_pair(loop, cfg, frames, mode=mode, nchunks=8)
+            out[name] = cmds
+            if kw:
+                t = loop.get_timing(3, timeout_us=WAIT_US)
+                assert 0 < t["latency_us"] <= t["frame_us"] and t["polc_us"] > 0
+                if "stage_timing" in kw:
+                    assert t["slopes_us"] > 0 and t["mvm_us"] > 0
+                else:
+                    assert t["slopes_us"] == -1 and t["mvm_us"] == -1
+    for a, b, c in zip(out["overlap"], out["serial"], out["plain"]):
+        assert np.array_equal(a, b) and np.array_equal(a, c)
