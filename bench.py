@@ -236,11 +236,24 @@ def run_unpaced_timed(loop, dev_frames, steps, warmup, sampler, first_id):
     return rows, fid
 
 
-def run_host_path(loop, host_frames, plans, steps, warmup, sampler, first_id, paced):
+def run_host_path(loop, host_frames, plans, steps, warmup, sampler, first_id, paced, swap=None):
     """Frames from page-locked host memory through rtc_submit_pixels (row chunks of all
     cameras interleaved) and rtc_get_commands.  Unpaced: latency = first submit -> commands
     returned.  Paced at the MCAO frame rate with the readout spread over the chunks:
-    latency = last chunk submitted (last pixel in) -> commands returned."""
+    latency = last chunk submitted (last pixel in) -> commands returned.
+    swap = (seconds, kwargs): a background thread calls loop.update(**kwargs) every that
+    many seconds during the timed frames (the paper's parameter-swap experiment); the
+    frames that applied a swap are reported apart."""
+    upd_times, swap_lat, stop = [], [], threading.Event()
+
+    def updater():
+        while not stop.wait(swap[0]):
+            t0 = time.perf_counter()
+            loop.update(**swap[1])
+            upd_times.append(time.perf_counter() - t0)
+
+    th = threading.Thread(target=updater, daemon=True) if swap else None
+    swaps_seen = loop.info()["swaps"] if swap else 0
     period = 1.0 / PACED_HZ
     nch = max(len(p) for p in plans)
     dt = READOUT_MS * 1e-3 / nch
@@ -272,12 +285,25 @@ def run_host_path(loop, host_frames, plans, steps, warmup, sampler, first_id, pa
         t_done = time.perf_counter()
         if timed:
             lat.append(((t_done - t_last) if paced else (t_done - t_first)) * 1e6)
+            if th is not None:
+                if k == warmup:
+                    th.start()
+                sw = loop.info()["swaps"]
+                if sw != swaps_seen:
+                    swap_lat.append(lat.pop())
+                    swaps_seen = sw
         fid += 1
         t_next += period
         if paced and time.perf_counter() > t_next:
             t_next = time.perf_counter() + 0.0005
     sampler.mark(False)
     gc.enable()
+    if th is not None:
+        stop.set()
+        th.join()
+        return lat, fid, {"updates": len(upd_times), "swap_frames": len(swap_lat),
+                          "upload_s_mean": float(np.mean(upd_times)) if upd_times else None,
+                          "latency_us_swap_frames": stats(swap_lat) if swap_lat else None}
     return lat, fid
 
 
@@ -305,11 +331,13 @@ def run_host_frames(loop, host_frames, steps, warmup, sampler, first_id):
 
 
 def cpu_oracle(cfg, frames, nframes=3):
+    """The oracle on the first nframes + 1 frames of the ring (the same frames, in the same
+    order, as the parity loop): returns the per-frame times and commands of frames 2.."""
     from oracle import OracleLoop
     t0 = time.perf_counter()
     ref = OracleLoop(cfg)
     t_setup = time.perf_counter() - t0
-    ref.step(frames[0])                       # warm-up frame
+    ref.step(frames[0])                       # warm-up frame (frame 1 of the parity loop)
     times, cmds = [], []
     for k in range(nframes):
         t0 = time.perf_counter()
@@ -402,7 +430,7 @@ def ours_arm(args, world, rank, local):
         cfgs = {"f32": cfg, "bf16": bcfg}
         for name in ("f32", "bf16"):
             # latency loops: the MVM starts while the slope kernel runs (frame-level events only)
-            loops[name] = rtc.Loop(cfgs[name], device=local, timing=True, telemetry=True)
+            loops[name] = rtc.Loop(cfgs[name], device=local, timing=True, telemetry=True, updatable=(name == "f32"))
             # stage loops: slope and MVM kernels timed separately (serialised) for the MVM bandwidth
             loops[name + "_stage"] = rtc.Loop(cfgs[name], device=local, stage_timing=True, telemetry=True)
         fid = 1
@@ -419,9 +447,13 @@ def ours_arm(args, world, rank, local):
         # 3) camera-paced last-pixel latency (the paper's definition), FP32 and BF16
         paced = {}
         for name in ("f32", "bf16"):
-            lat, fid = run_host_path(loops[name], host_frames, plans, args.steps, args.warmup, sampler, fid,
-                                     paced=True)
+            lat, fid = run_host_path(loops[name], host_frames, plans, args.paced_frames, args.paced_warmup, sampler,
+                                     fid, paced=True)
             paced[name] = stats(lat)
+        # 4) the same paced FP32 loop while the whole control matrix is re-uploaded and swapped every second
+        lat, fid, swap_info = run_host_path(loops["f32"], host_frames, plans, args.swap_frames, args.paced_warmup,
+                                            sampler, fid, paced=True, swap=(1.0, {"M": cfg["M"]}))
+        swap_info["latency_us_other_frames"] = stats(lat)
         infos = {n: loops[n].info() for n in loops}
     finally:
         sampler.stop()
@@ -435,19 +467,21 @@ def ours_arm(args, world, rank, local):
     cpu = None
     parity = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        times, cmds_ref, _ = cpu_oracle(cfg, frames, nframes=3)
+        n_or = args.parity_frames
+        times, cmds_ref, _ = cpu_oracle(cfg, frames, nframes=n_or)
         cpu = {"value": statistics.median(times), "unit": "us", "cores": 1, "kind": "oracle",
-               "sample": "3 full MCAO frames (after 1 warm-up frame) through the float64 numpy oracle on 1 host "
-                         "thread; same seeded frames and matrices"}
+               "sample": f"{n_or} full MCAO frames (after 1 warm-up frame) through the float64 numpy oracle on 1 "
+                         "host thread; same seeded frames and matrices"}
         with rtc.Loop(cfg, device=local) as chk:
             errs = []
-            for k in range(4):
-                chk.process_frame(k + 1, dev_frames[k])
+            for k in range(n_or + 1):
+                chk.process_frame(k + 1, dev_frames[k % len(dev_frames)])
                 _, a = chk.get_commands(timeout_us=10_000_000)
                 if k >= 1:
                     r = cmds_ref[k - 1]
                     errs.append(float(np.max(np.abs(a - r)) / np.max(np.abs(r))))
-        parity = {"frames": len(errs), "max_rel_err_commands": max(errs), "tol": 1e-5}
+        parity = {"frames": len(errs), "max_rel_err_commands": max(errs), "tol": 1e-5,
+                  "norm": "max|a - a_oracle| / max|a_oracle| per frame, FP32 path, float64 oracle"}
     for l in loops.values():
         l.close()
 
@@ -477,7 +511,11 @@ def ours_arm(args, world, rank, local):
         "mvm_frac_of_hbm": {"f32": gbs["f32"] / peak, "bf16": gbs["bf16"] / peak, "peak": f"{peak_kind} {peak} GB/s"},
         "paced": {"definition": "last chunk submitted (last pixel in) -> commands returned, host clock; "
                                 f"{PACED_HZ:.0f} Hz, {READOUT_MS} ms readout over {NCHUNKS} row chunks per LGS camera, "
-                                "pixels from page-locked host memory", **paced},
+                                f"pixels from page-locked host memory; {args.paced_frames} frames after "
+                                f"{args.paced_warmup} warm-up frames per format", **paced},
+        "swap": {"definition": "paced FP32 frames while a second thread re-uploads the 1.67 GB control matrix "
+                               "into the shadow buffer every 1 s (rtc_update); the first frame after each upload "
+                               "swaps pointers at its start (Section 3.2's double buffer)", **swap_info},
         "e2e": {"value": vals[2], "unit": "us", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": 4 * (infos["f32"]["na"] + infos["f32"]["ns"]),
                 "definition": "rtc_process_frame entry -> rtc_get_commands returned, host clock, unpaced; frames in "
@@ -529,6 +567,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--paced-frames", type=int, default=10000, help="camera-paced frames per matrix format")
+    ap.add_argument("--paced-warmup", type=int, default=500)
+    ap.add_argument("--parity-frames", type=int, default=20, help="frames checked against the FP64 oracle")
+    ap.add_argument("--swap-frames", type=int, default=2500, help="paced frames of the parameter-swap run")
     ap.add_argument("--workload", default="mcao", help="configuration (profiling aid; the bench line is mcao)")
     ap.add_argument("--quick", action="store_true", help="profiling aid: only the unpaced loop")
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "e4m3"], help="matrix storage for --quick")

@@ -67,6 +67,8 @@ extern "C" {
 #define RTC_FLAG_TELEMETRY  2u /* copy slopes of every frame to the page-locked ring */
 #define RTC_FLAG_STAGE_TIMING 4u /* also time the slope and MVM kernels separately; this
                                     serialises them (no early start of the MVM) */
+#define RTC_FLAG_UPDATABLE  8u /* keep shadow copies of the parameters for rtc_update
+                                  (twice the matrix memory) */
 
 #define RTC_MAX_WFS 16
 
@@ -234,6 +236,42 @@ typedef struct rtc_timing {
 } rtc_timing;
 int rtc_get_timing(rtc_loop* loop, uint64_t frame_id, rtc_timing* out, int64_t timeout_us);
 
+/* ---- parameter double buffer (Section 3.2) ----------------------------- */
+
+/* New parameters for a running loop.  Every pointer may be NULL (unchanged);
+ * shapes and element types are those given at creation.  M: host row-major
+ * na x ns in the loop's matrix type, with M_scale (float32[na]) when the loop
+ * was created with row scales (NULL keeps the current scales).  P / P_scale:
+ * the same for the POLC matrix (loop created with POLC).  dark / flat: arrays
+ * of nwfs host pointers (entries may be NULL).  threshold: nwfs values or NULL.
+ * ref_slopes: ns values.  set_control non-zero replaces gain, leak and the clip. */
+typedef struct rtc_update_desc {
+    const void* M;
+    const float* M_scale;
+    const void* P;
+    const float* P_scale;
+    const float* const* dark;
+    const float* const* flat;
+    const float* threshold;
+    const float* ref_slopes;
+    int32_t set_control;
+    float gain, leak;
+    int32_t clip;
+    float amin, amax;
+} rtc_update_desc;
+
+/* Parameter change without stopping the loop, as DARC's double buffer
+ * (Section 3.2): the new values are copied into shadow buffers on a separate
+ * low-priority stream while frames keep running, then the first frame that
+ * starts after this call returns uses them (the swap is a host-side pointer
+ * exchange at the frame boundary, with no work added to that frame on the
+ * GPU).  The POLC term that frame uses was computed with the previous P; the
+ * new P applies from that frame's own POLC product on.  Blocks the calling
+ * thread (not the submitting one) until the upload is done; a second call
+ * before the swap replaces the pending values.  Needs RTC_FLAG_UPDATABLE;
+ * RTC_EINVAL for bad arguments or NaN/Inf values (nothing is swapped then). */
+int rtc_update(rtc_loop* loop, const rtc_update_desc* desc);
+
 /* ---- state and introspection ---------------------------------------- */
 
 /* Wait for queued work, then copy the integrator state a (na floats) out. */
@@ -255,6 +293,7 @@ typedef struct rtc_info {
     uint64_t pixel_bytes;      /* raw + calibration bytes read per frame by the slope kernels */
     uint64_t device_bytes;     /* device memory held by the loop */
     uint64_t frames_done, frames_dropped, frames_overrun;
+    uint64_t swaps;            /* parameter swaps applied (rtc_update) */
 } rtc_info;
 int rtc_get_info(rtc_loop* loop, rtc_info* out);
 

@@ -22,7 +22,7 @@ RTC_EORDER, RTC_EDROPPED, RTC_ECUDA, RTC_ENOENT = -4, -5, -6, -7
 RTC_WFS_SH, RTC_WFS_PYRAMID = 0, 1
 RTC_F32, RTC_BF16, RTC_E4M3 = 0, 1, 2
 RTC_THRESH_SUBTRACT, RTC_THRESH_CLIP = 0, 1
-RTC_FLAG_TIMING, RTC_FLAG_TELEMETRY, RTC_FLAG_STAGE_TIMING = 1, 2, 4
+RTC_FLAG_TIMING, RTC_FLAG_TELEMETRY, RTC_FLAG_STAGE_TIMING, RTC_FLAG_UPDATABLE = 1, 2, 4, 8
 RTC_MAX_WFS = 16
 DTYPES = {"f32": RTC_F32, "bf16": RTC_BF16, "e4m3": RTC_E4M3}
 CODE_NP = {RTC_F32: np.float32, RTC_BF16: np.uint16, RTC_E4M3: np.uint8}
@@ -71,12 +71,19 @@ class rtc_timing(C.Structure):
                 ("frame_us", C.c_float)]
 
 
+class rtc_update_desc(C.Structure):
+    _fields_ = [("M", C.c_void_p), ("M_scale", f32p), ("P", C.c_void_p), ("P_scale", f32p),
+                ("dark", C.POINTER(f32p)), ("flat", C.POINTER(f32p)), ("threshold", f32p), ("ref_slopes", f32p),
+                ("set_control", C.c_int32), ("gain", C.c_float), ("leak", C.c_float), ("clip", C.c_int32),
+                ("amin", C.c_float), ("amax", C.c_float)]
+
+
 class rtc_info(C.Structure):
     _fields_ = [("na", C.c_int32), ("ns", C.c_int32), ("nwfs", C.c_int32), ("nblocks", C.c_int32),
                 ("nrows", C.c_int32), ("m_dtype", C.c_int32), ("p_dtype", C.c_int32),
                 ("m_bytes", C.c_uint64), ("p_bytes", C.c_uint64), ("pixel_bytes", C.c_uint64),
                 ("device_bytes", C.c_uint64), ("frames_done", C.c_uint64), ("frames_dropped", C.c_uint64),
-                ("frames_overrun", C.c_uint64)]
+                ("frames_overrun", C.c_uint64), ("swaps", C.c_uint64)]
 
 
 # (name, restype, argtypes) of every entry point declared in include/rtc.h
@@ -89,6 +96,7 @@ SIGNATURES = [
     ("rtc_get_commands", C.c_int, [C.c_void_p, f32p, C.c_size_t, C.POINTER(C.c_uint64), C.c_int64]),
     ("rtc_get_telemetry", C.c_int, [C.c_void_p, C.c_uint64, f32p, C.c_size_t, f32p, C.c_size_t, C.c_int64]),
     ("rtc_get_timing", C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(rtc_timing), C.c_int64]),
+    ("rtc_update", C.c_int, [C.c_void_p, C.POINTER(rtc_update_desc)]),
     ("rtc_get_state", C.c_int, [C.c_void_p, f32p, C.c_size_t]),
     ("rtc_set_state", C.c_int, [C.c_void_p, f32p, C.c_size_t]),
     ("rtc_sync", C.c_int, [C.c_void_p]),
@@ -157,7 +165,7 @@ def _pitch(x):
 class Loop:
     """One AO loop on one GPU, built from a configuration dict (see synth)."""
 
-    def __init__(self, cfg, device=0, timing=False, telemetry=False, ring=4, stage_timing=False):
+    def __init__(self, cfg, device=0, timing=False, telemetry=False, ring=4, stage_timing=False, updatable=False):
         self.cfg = cfg
         self.na = int(cfg["na"])
         wl = cfg["wfs"]
@@ -189,7 +197,7 @@ class Loop:
             darks[k] = _fptr(d)
             flats[k] = _fptr(f)
         flags = ((RTC_FLAG_TIMING if timing or stage_timing else 0) | (RTC_FLAG_TELEMETRY if telemetry else 0)
-                 | (RTC_FLAG_STAGE_TIMING if stage_timing else 0))
+                 | (RTC_FLAG_STAGE_TIMING if stage_timing else 0) | (RTC_FLAG_UPDATABLE if updatable else 0))
         geo = rtc_geometry(len(wl), warr, device, flags, ring)
         ref = _f32(cfg.get("ref_slopes"))
         cal = rtc_calib(darks, flats, thr.ctypes.data_as(f32p), mode.ctypes.data_as(C.POINTER(C.c_int32)), _fptr(ref))
@@ -279,6 +287,45 @@ class Loop:
         t = rtc_timing()
         _check(lib.rtc_get_timing(self._h, frame_id, C.byref(t), int(timeout_us)), self._h)
         return {k: getattr(t, k) for k, _ in rtc_timing._fields_}
+
+    # -- parameter double buffer ---------------------------------------------
+    def update(self, M=None, M_scale=None, P=None, P_scale=None, dark=None, flat=None, threshold=None,
+               ref_slopes=None, control=None):
+        """rtc_update: stage new parameters; the next frame to start uses them.
+        dark / flat: dicts {wfs index: map}; control: (gain, leak, clip or None)."""
+        keep = []
+
+        def arr(x, dt):
+            if x is None:
+                return None
+            a = np.ascontiguousarray(x, dtype=dt)
+            keep.append(a)
+            return a
+
+        mdt = CODE_NP[DTYPES[self.cfg.get("M_dtype", "f32")]]
+        pdt = CODE_NP[DTYPES[self.cfg.get("P_dtype", "f32")]]
+        Ma, Pa = arr(M, mdt), arr(P, pdt)
+        d = rtc_update_desc()
+        d.M = None if Ma is None else Ma.ctypes.data
+        d.M_scale = _fptr(arr(M_scale, np.float32))
+        d.P = None if Pa is None else Pa.ctypes.data
+        d.P_scale = _fptr(arr(P_scale, np.float32))
+        nw = len(self.cfg["wfs"])
+        for name, maps in (("dark", dark), ("flat", flat)):
+            if maps:
+                ptrs = (f32p * nw)()
+                for k, m in maps.items():
+                    ptrs[k] = _fptr(arr(m, np.float32))
+                keep.append(ptrs)
+                setattr(d, name, ptrs)
+        d.threshold = _fptr(arr(threshold, np.float32))
+        d.ref_slopes = _fptr(arr(ref_slopes, np.float32))
+        if control is not None:
+            g, l, clip = control
+            d.set_control, d.gain, d.leak = 1, float(g), float(l)
+            if clip:
+                d.clip, d.amin, d.amax = 1, float(clip[0]), float(clip[1])
+        _check(lib.rtc_update(self._h, C.byref(d)), self._h)
 
     # -- state ----------------------------------------------------------------
     def get_state(self):

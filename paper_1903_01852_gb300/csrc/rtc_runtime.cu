@@ -111,12 +111,37 @@ struct rtc_loop {
     std::deque<int> pending;
     uint64_t frames_done = 0, frames_dropped = 0, frames_overrun = 0;
 
+    // parameter double buffer (rtc_update): shadow copies, swapped at a frame boundary
+    bool updatable = false;
+    void* sh_M = nullptr;
+    float* sh_Mscale = nullptr;
+    void* sh_P = nullptr;
+    float* sh_Pscale = nullptr;
+    std::vector<float*> sh_dark, sh_flat;
+    float* sh_ref = nullptr;
+    WfsDev* sh_wfs = nullptr;
+    std::vector<WfsDev> wfs_host;           // the active WFS table as last uploaded
+    cudaStream_t st_up = nullptr;
+    cudaEvent_t ev_swap = nullptr;
+    bool swap_ev_valid = false;
+    std::mutex upd_mu;                      // held by rtc_update; the submitting thread only try-locks it
+    bool upd_pending = false;
+    unsigned upd_mask = 0;                  // kUpd* bits of items waiting in the shadow buffers
+    std::vector<char> upd_dark, upd_flat;   // per WFS
+    std::vector<WfsDev> upd_table;          // WFS table after the swap
+    bool upd_ctrl = false;
+    float upd_gain = 0.f, upd_leak = 0.f, upd_amin = 0.f, upd_amax = 0.f;
+    int upd_clip = 0;
+    uint64_t swaps = 0;
+
     std::string err;
     bool broken = false;
     bool cuda_touched = false;   // false until creation first calls into CUDA
 };
 
 namespace {
+
+enum : unsigned { kUpdM = 1u, kUpdMscale = 2u, kUpdP = 4u, kUpdPscale = 8u, kUpdTable = 16u, kUpdRef = 32u };
 
 int fail(rtc_loop* L, int code, const std::string& msg) {
     if (L) L->err = msg;
@@ -186,8 +211,11 @@ void release(rtc_loop* L) {
     for (void* p : L->allocs) cudaFree(p);
     if (L->h_ring) cudaFreeHost(L->h_ring);
     if (L->h_done) cudaFreeHost(L->h_done);
+    if (L->st_up) cudaStreamSynchronize(L->st_up);
+    if (L->ev_swap) cudaEventDestroy(L->ev_swap);
     if (L->st) cudaStreamDestroy(L->st);
     if (L->st_tel) cudaStreamDestroy(L->st_tel);
+    if (L->st_up) cudaStreamDestroy(L->st_up);
     cudaGetLastError();
     delete L;
 }
@@ -265,6 +293,7 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
     L->dev = G->device;
     L->flags = G->flags;
     L->stage_timing = (G->flags & RTC_FLAG_STAGE_TIMING) != 0;
+    L->updatable = (G->flags & RTC_FLAG_UPDATABLE) != 0;
     L->timing = (G->flags & RTC_FLAG_TIMING) != 0 || L->stage_timing;
     L->telemetry = (G->flags & RTC_FLAG_TELEMETRY) != 0;
     L->ring = G->ring > 0 ? G->ring : 4;
@@ -430,6 +459,11 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
     if (L->has_polc) need += (size_t)L->na * round_up(L->na, VP) * dtype_size(L->p_dtype) * 2;
     for (auto& w : L->wfs) need += (size_t)w.height * (round_up(w.width, 4) * 8 + round_up(w.width, 8) * 2);
     need += (size_t)L->nblk * L->na * 4 + (size_t)s_len * 4 + (size_t)a_len * 8;
+    if (L->updatable) {
+        need += L->m_bytes;
+        if (L->has_polc) need += (size_t)L->na * round_up(L->na, VP) * dtype_size(L->p_dtype);
+        for (auto& w : L->wfs) need += (size_t)w.height * round_up(w.width, 4) * 8;
+    }
     size_t free_b = 0, total_b = 0;
     CK(L, cudaMemGetInfo(&free_b, &total_b));
     if (need + (64u << 20) > free_b)
@@ -497,8 +531,38 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
         TRY(dev_alloc(L, &L->d_frame[k], (size_t)w.height * fp * 2));
         CK(L, cudaMemset(L->d_frame[k], 0, (size_t)w.height * fp * 2));
     }
+    if (L->updatable && !L->d_ref) {           // reference slopes become updatable: start from zeros
+        TRY(dev_alloc(L, &L->d_ref, (size_t)L->ns * 4));
+        CK(L, cudaMemset(L->d_ref, 0, (size_t)L->ns * 4));
+    }
     TRY(dev_alloc(L, &L->d_wfs, wdev.size() * sizeof(WfsDev)));
     CK(L, cudaMemcpy(L->d_wfs, wdev.data(), wdev.size() * sizeof(WfsDev), cudaMemcpyHostToDevice));
+    L->wfs_host = wdev;
+    if (L->updatable) {
+        TRY(dev_alloc(L, &L->sh_M, std::max<uint64_t>(L->m_bytes, 16)));
+        CK(L, cudaMemset(L->sh_M, 0, std::max<uint64_t>(L->m_bytes, 16)));
+        if (L->d_Mscale) TRY(dev_alloc(L, &L->sh_Mscale, (size_t)L->na * 4));
+        if (L->has_polc) {
+            TRY(dev_alloc(L, &L->sh_P, L->p_bytes));
+            CK(L, cudaMemset(L->sh_P, 0, L->p_bytes));
+            if (L->d_Pscale) TRY(dev_alloc(L, &L->sh_Pscale, (size_t)L->na * 4));
+        }
+        L->sh_dark.resize(L->nwfs);
+        L->sh_flat.resize(L->nwfs);
+        for (int k = 0; k < L->nwfs; ++k) {
+            const size_t bytes = (size_t)L->wfs[k].height * round_up(L->wfs[k].width, 4) * 4;
+            TRY(dev_alloc(L, &L->sh_dark[k], bytes));
+            TRY(dev_alloc(L, &L->sh_flat[k], bytes));
+            CK(L, cudaMemset(L->sh_dark[k], 0, bytes));
+            CK(L, cudaMemset(L->sh_flat[k], 0, bytes));
+        }
+        TRY(dev_alloc(L, &L->sh_ref, (size_t)L->ns * 4));
+        TRY(dev_alloc(L, &L->sh_wfs, wdev.size() * sizeof(WfsDev)));
+        CK(L, cudaStreamCreateWithPriority(&L->st_up, cudaStreamNonBlocking, 0));
+        CK(L, cudaEventCreateWithFlags(&L->ev_swap, cudaEventDisableTiming));
+        L->upd_dark.assign(L->nwfs, 0);
+        L->upd_flat.assign(L->nwfs, 0);
+    }
     TRY(dev_alloc(L, &L->d_rows, rows.size() * sizeof(SlopeRow)));
     CK(L, cudaMemcpy(L->d_rows, rows.data(), rows.size() * sizeof(SlopeRow), cudaMemcpyHostToDevice));
     TRY(dev_alloc(L, &L->d_parts, parts.size() * sizeof(SlopePart)));
@@ -574,6 +638,45 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
     L->rows_done.assign(L->nwfs, 0);
     L->blks_done.assign(L->nwfs, 0);
     CK(L, cudaStreamSynchronize(L->st));
+    return RTC_OK;
+}
+
+// Frame boundary: exchange the active and shadow pointers of every item a
+// finished rtc_update left pending (no GPU work), and remember where the old
+// buffers stop being read.  Skipped while an update is still uploading.
+int apply_pending_update(rtc_loop* L) {
+    if (!L->updatable) return RTC_OK;
+    std::unique_lock<std::mutex> g(L->upd_mu, std::try_to_lock);
+    if (!g.owns_lock() || !L->upd_pending) return RTC_OK;
+    const unsigned m = L->upd_mask;
+    if (m & kUpdM) std::swap(L->d_M, L->sh_M);
+    if (m & kUpdMscale) std::swap(L->d_Mscale, L->sh_Mscale);
+    if (m & kUpdP) std::swap(L->d_P, L->sh_P);
+    if (m & kUpdPscale) std::swap(L->d_Pscale, L->sh_Pscale);
+    if (m & kUpdRef) std::swap(L->d_ref, L->sh_ref);
+    if (m & kUpdTable) {
+        for (int k = 0; k < L->nwfs; ++k) {
+            if (L->upd_dark[k]) std::swap(L->d_dark[k], L->sh_dark[k]);
+            if (L->upd_flat[k]) std::swap(L->d_flat[k], L->sh_flat[k]);
+        }
+        std::swap(L->d_wfs, L->sh_wfs);
+        L->wfs_host = L->upd_table;
+    }
+    if (L->upd_ctrl) {
+        L->gain = L->upd_gain;
+        L->leak = L->upd_leak;
+        L->clip = L->upd_clip;
+        L->amin = L->upd_amin;
+        L->amax = L->upd_amax;
+    }
+    std::fill(L->upd_dark.begin(), L->upd_dark.end(), 0);
+    std::fill(L->upd_flat.begin(), L->upd_flat.end(), 0);
+    L->upd_mask = 0;
+    L->upd_ctrl = false;
+    L->upd_pending = false;
+    ++L->swaps;
+    CK(L, cudaEventRecord(L->ev_swap, L->st));   // frames before this point read the old buffers
+    L->swap_ev_valid = true;
     return RTC_OK;
 }
 
@@ -714,6 +817,7 @@ int submit_impl(rtc_loop* L, const rtc_chunk* c) {
     if (!L->active) {
         if (L->have_last && c->frame_id <= L->last_id) return fail(L, RTC_EORDER, "frame id not increasing");
         if (c->row_begin != 0) return fail(L, RTC_EORDER, "a frame must start at row 0");
+        TRY(apply_pending_update(L));
         begin_frame(L, c->frame_id, true);
         if (L->timing) CK(L, cudaEventRecord(L->slots[L->cur_slot].ev_start, L->st));
     } else if (c->row_begin != L->rows_in[c->wfs]) {
@@ -804,6 +908,7 @@ int process_impl(rtc_loop* L, uint64_t id, const uint16_t* const* px, const size
         status = RTC_EDROPPED;
         L->err = "frame " + std::to_string(L->cur_id) + " was incomplete and has been dropped";
     }
+    TRY(apply_pending_update(L));
     begin_frame(L, id, false);
     Slot& s = L->slots[L->cur_slot];
     if (L->timing) {
@@ -976,6 +1081,108 @@ int rtc_get_timing(rtc_loop* L, uint64_t frame_id, rtc_timing* out, int64_t time
     return RTC_OK;
 }
 
+int rtc_update(rtc_loop* L, const rtc_update_desc* d) {
+    if (!L || !d) return fail(L, RTC_EINVAL, "loop and desc are required");
+    if (!L->updatable) return fail(L, RTC_EINVAL, "loop created without RTC_FLAG_UPDATABLE");
+    if ((d->P || d->P_scale) && !L->has_polc) return fail(L, RTC_EINVAL, "loop has no POLC matrix");
+    if (d->M_scale && !L->d_Mscale) return fail(L, RTC_EINVAL, "loop was created without control-matrix row scales");
+    if (d->P_scale && !L->d_Pscale) return fail(L, RTC_EINVAL, "loop was created without POLC row scales");
+    // validate everything before touching any buffer
+    if (d->M && L->m_dtype == RTC_F32 && !all_finite(static_cast<const float*>(d->M), (size_t)L->na * L->ns))
+        return fail(L, RTC_EINVAL, "new control matrix not finite");
+    if (d->P && L->p_dtype == RTC_F32 && !all_finite(static_cast<const float*>(d->P), (size_t)L->na * L->na))
+        return fail(L, RTC_EINVAL, "new POLC matrix not finite");
+    if (d->M_scale && !all_finite(d->M_scale, L->na)) return fail(L, RTC_EINVAL, "new M_scale not finite");
+    if (d->P_scale && !all_finite(d->P_scale, L->na)) return fail(L, RTC_EINVAL, "new P_scale not finite");
+    if (d->ref_slopes && !all_finite(d->ref_slopes, L->ns)) return fail(L, RTC_EINVAL, "new ref_slopes not finite");
+    for (int k = 0; k < L->nwfs; ++k) {
+        const size_t n = (size_t)L->wfs[k].width * L->wfs[k].height;
+        if (d->dark && d->dark[k] && !all_finite(d->dark[k], n)) return fail(L, RTC_EINVAL, "new dark not finite");
+        if (d->flat && d->flat[k] && !all_finite(d->flat[k], n)) return fail(L, RTC_EINVAL, "new flat not finite");
+        if (d->threshold && !(d->threshold[k] >= 0.f && std::isfinite(d->threshold[k])))
+            return fail(L, RTC_EINVAL, "new threshold must be finite and >= 0");
+    }
+    if (d->set_control && (!std::isfinite(d->gain) || !std::isfinite(d->leak) || (d->clip && !(d->amin <= d->amax))))
+        return fail(L, RTC_EINVAL, "bad control parameters");
+
+    std::lock_guard<std::mutex> g(L->upd_mu);
+    TRY(use_device(L));
+    // the shadow buffers may still be read by frames issued before the last swap
+    if (L->swap_ev_valid) CK(L, cudaStreamWaitEvent(L->st_up, L->ev_swap, 0));
+    const size_t esz = dtype_size(L->m_dtype);
+    unsigned mask = 0;
+    if (d->M) {
+        for (const BlockDev& B : L->blocks_h)
+            if (B.ncols)
+                CK(L, cudaMemcpy2DAsync(static_cast<uint8_t*>(L->sh_M) + (size_t)B.m_off * esz, (size_t)B.pitch * esz,
+                                        static_cast<const uint8_t*>(d->M) + (size_t)B.c0 * esz, (size_t)L->ns * esz,
+                                        (size_t)B.ncols * esz, L->na, cudaMemcpyHostToDevice, L->st_up));
+        mask |= kUpdM;
+    }
+    if (d->M_scale) {
+        CK(L, cudaMemcpyAsync(L->sh_Mscale, d->M_scale, (size_t)L->na * 4, cudaMemcpyHostToDevice, L->st_up));
+        mask |= kUpdMscale;
+    }
+    if (d->P) {
+        const size_t pe = dtype_size(L->p_dtype);
+        const size_t pitch = round_up((size_t)L->na, elems_per_16B(L->p_dtype));
+        CK(L, cudaMemcpy2DAsync(L->sh_P, pitch * pe, d->P, (size_t)L->na * pe, (size_t)L->na * pe, L->na,
+                                cudaMemcpyHostToDevice, L->st_up));
+        mask |= kUpdP;
+    }
+    if (d->P_scale) {
+        CK(L, cudaMemcpyAsync(L->sh_Pscale, d->P_scale, (size_t)L->na * 4, cudaMemcpyHostToDevice, L->st_up));
+        mask |= kUpdPscale;
+    }
+    if (d->ref_slopes) {
+        CK(L, cudaMemcpyAsync(L->sh_ref, d->ref_slopes, (size_t)L->ns * 4, cudaMemcpyHostToDevice, L->st_up));
+        mask |= kUpdRef;
+    }
+    bool table = (L->upd_mask & kUpdTable) != 0;
+    for (int k = 0; k < L->nwfs; ++k) {
+        const rtc_wfs& w = L->wfs[k];
+        const size_t cp = round_up(w.width, 4);
+        if (d->dark && d->dark[k]) {
+            CK(L, cudaMemcpy2DAsync(L->sh_dark[k], cp * 4, d->dark[k], (size_t)w.width * 4, (size_t)w.width * 4,
+                                    w.height, cudaMemcpyHostToDevice, L->st_up));
+            L->upd_dark[k] = 1;
+            table = true;
+        }
+        if (d->flat && d->flat[k]) {
+            CK(L, cudaMemcpy2DAsync(L->sh_flat[k], cp * 4, d->flat[k], (size_t)w.width * 4, (size_t)w.width * 4,
+                                    w.height, cudaMemcpyHostToDevice, L->st_up));
+            L->upd_flat[k] = 1;
+            table = true;
+        }
+    }
+    if (d->threshold) table = true;
+    if (table) {
+        // the WFS table as it will be after the swap
+        std::vector<WfsDev> t = (L->upd_mask & kUpdTable) ? L->upd_table : L->wfs_host;
+        for (int k = 0; k < L->nwfs; ++k) {
+            t[k].dark = L->upd_dark[k] ? L->sh_dark[k] : L->d_dark[k];
+            t[k].flat = L->upd_flat[k] ? L->sh_flat[k] : L->d_flat[k];
+            if (d->threshold) t[k].threshold = d->threshold[k];
+        }
+        L->upd_table = t;
+        CK(L, cudaMemcpyAsync(L->sh_wfs, L->upd_table.data(), t.size() * sizeof(WfsDev), cudaMemcpyHostToDevice,
+                              L->st_up));
+        mask |= kUpdTable;
+    }
+    CK(L, cudaStreamSynchronize(L->st_up));
+    if (d->set_control) {
+        L->upd_ctrl = true;
+        L->upd_gain = d->gain;
+        L->upd_leak = d->leak;
+        L->upd_clip = d->clip;
+        L->upd_amin = d->amin;
+        L->upd_amax = d->amax;
+    }
+    L->upd_mask |= mask;
+    L->upd_pending = L->upd_mask != 0 || L->upd_ctrl;
+    return RTC_OK;
+}
+
 int rtc_get_state(rtc_loop* L, float* a, size_t na) {
     if (!L || !a || na != (size_t)L->na) return fail(L, RTC_EINVAL, "a must hold na floats");
     TRY(use_device(L));
@@ -1027,6 +1234,7 @@ int rtc_get_info(rtc_loop* L, rtc_info* out) {
     out->frames_done = L->frames_done;
     out->frames_dropped = L->frames_dropped;
     out->frames_overrun = L->frames_overrun;
+    out->swaps = L->swaps;
     return RTC_OK;
 }
 

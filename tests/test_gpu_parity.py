@@ -364,3 +364,77 @@ def test_overlapped_and_serialised_launches_give_identical_commands(rtc, torch_c
                     assert t["slopes_us"] == -1 and t["mvm_us"] == -1
     for a, b, c in zip(out["overlap"], out["serial"], out["plain"]):
         assert np.array_equal(a, b) and np.array_equal(a, c)
+
+
+# ------------------------------------------------------------------ parameter double buffer
+
+def test_parameter_swap_takes_effect_at_the_next_frame(rtc, torch_cuda):
+    from oracle import stored_matrix
+    cfg = ragged_config(seed=121)
+    rng = np.random.default_rng(122)
+    new = ragged_config(seed=123)                 # same geometry, new matrices, maps and references
+    new["wfs"][2]["threshold"] = 7.5
+    new["gain"], new["leak"], new["clip"] = 0.3, 0.05, (-0.2, 0.25)
+    frames = synth.draw_frames(cfg, 7, seed=124)
+    ref = OracleLoop(cfg)
+    with rtc.Loop(cfg, telemetry=True, updatable=True) as loop:
+        for k in range(3):
+            loop.submit_frame(k + 1, frames[k])
+            a = loop.get_commands(timeout_us=WAIT_US)[1]
+            assert rel(a, ref.step(frames[k])[1]) <= TOL_F32
+        loop.update(M=new["M"], P=new["P"], dark={0: new["wfs"][0]["dark"], 3: new["wfs"][3]["dark"]},
+                    flat={1: new["wfs"][1]["flat"]}, threshold=[w["threshold"] for w in new["wfs"]],
+                    ref_slopes=new["ref_slopes"], control=(new["gain"], new["leak"], new["clip"]))
+        # the oracle switches at the same frame boundary; q was computed with the old P
+        cfg2 = dict(cfg, M=new["M"], P=new["P"], ref_slopes=new["ref_slopes"], gain=new["gain"],
+                    leak=new["leak"], clip=new["clip"])
+        cfg2["wfs"] = [dict(w) for w in cfg["wfs"]]
+        cfg2["wfs"][0]["dark"] = new["wfs"][0]["dark"]
+        cfg2["wfs"][3]["dark"] = new["wfs"][3]["dark"]
+        cfg2["wfs"][1]["flat"] = new["wfs"][1]["flat"]
+        for k, w in enumerate(cfg2["wfs"]):
+            w["threshold"] = new["wfs"][k]["threshold"]
+        ref.cfg = cfg2
+        ref.m = stored_matrix(new["M"], "f32", None)
+        ref.p = stored_matrix(new["P"], "f32", None)
+        for k in range(3, 7):
+            loop.submit_frame(k + 1, frames[k])
+            fid, a = loop.get_commands(timeout_us=WAIT_US)
+            s, _ = loop.get_telemetry(fid, timeout_us=WAIT_US)
+            s_ref, a_ref = ref.step(frames[k])
+            assert rel(s, s_ref) <= TOL_F32 and rel(a, a_ref) <= TOL_F32, k
+        assert loop.info()["swaps"] == 1
+
+
+def test_update_while_frames_run_and_rejected_updates(rtc, torch_cuda):
+    import threading
+    cfg = synth.make_config("elt_scao_sh", polc=True)
+    frames = synth.draw_frames(cfg, 2, seed=125)
+    M2 = (cfg["M"] * np.float32(0.5)).astype(np.float32)
+    with rtc.Loop(cfg, telemetry=True, updatable=True) as loop, rtc.Loop(cfg) as plain:
+        with pytest.raises(rtc.RtcError) as e:
+            plain.update(M=M2)                                  # not created updatable
+        assert e.value.code == rtc.RTC_EINVAL
+        bad = M2.copy()
+        bad[5, 7] = np.inf
+        with pytest.raises(rtc.RtcError) as e:
+            loop.update(M=bad)
+        assert e.value.code == rtc.RTC_EINVAL
+        # upload on another thread while this thread keeps submitting frames
+        t = threading.Thread(target=loop.update, kwargs=dict(M=M2))
+        t.start()
+        fid = 1
+        while t.is_alive() or fid < 5:
+            loop.submit_frame(fid, frames[fid % 2])
+            loop.get_commands(timeout_us=WAIT_US)
+            fid += 1
+        t.join()
+        state_before = loop.get_state()
+        loop.submit_frame(fid, frames[fid % 2])          # starts after the update returned: uses M2
+        a_new = loop.get_commands(timeout_us=WAIT_US)[1]
+        assert loop.info()["swaps"] == 1
+    # replay that frame on a fresh loop built with M2, from the same integrator state
+    with rtc.Loop(dict(cfg, M=M2)) as chk:
+        chk.set_state(state_before)
+        chk.submit_frame(1, frames[fid % 2])
+        assert np.array_equal(chk.get_commands(timeout_us=WAIT_US)[1], a_new)
