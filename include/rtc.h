@@ -69,6 +69,9 @@ extern "C" {
                                     serialises them (no early start of the MVM) */
 #define RTC_FLAG_UPDATABLE  8u /* keep shadow copies of the parameters for rtc_update
                                   (twice the matrix memory) */
+#define RTC_FLAG_GRAPHS    16u /* page-locked input frames per ring slot and one captured CUDA
+                                  graph per slot (rtc_next_frame_buffers, rtc_submit_frame_graph);
+                                  excludes RTC_FLAG_UPDATABLE */
 
 #define RTC_MAX_WFS 16
 
@@ -206,6 +209,19 @@ int rtc_submit_pixels(rtc_loop* loop, const rtc_chunk* chunk);
 int rtc_process_frame(rtc_loop* loop, uint64_t frame_id,
                       const uint16_t* const* px, const size_t* pitch);
 
+/* Graph mode (RTC_FLAG_GRAPHS): the page-locked buffers, one per WFS (px[w],
+ * rows pitch[w] bytes apart, host addresses the GPU reads in place over the
+ * CPU-GPU link), into which the caller writes the next frame; waits until
+ * the GPU has finished the frame that last used them.  Valid until the next
+ * rtc_submit_frame_graph. */
+int rtc_next_frame_buffers(rtc_loop* loop, uint16_t** px, size_t* pitch);
+
+/* Graph mode: launch the CUDA graph captured at creation for the buffers the
+ * last rtc_next_frame_buffers returned (slopes, MVM with finalisation, POLC,
+ * telemetry: one launch instead of four kernels and their events).  Frame-id
+ * rules as rtc_process_frame. */
+int rtc_submit_frame_graph(rtc_loop* loop, uint64_t frame_id);
+
 /* Wait (busy-polling, up to timeout_us microseconds; <0 waits forever) for
  * the oldest frame whose pixels are all submitted and whose commands have not
  * yet been returned, then copy its na commands to out (host) and its frame
@@ -297,6 +313,13 @@ typedef struct rtc_info {
 } rtc_info;
 int rtc_get_info(rtc_loop* loop, rtc_info* out);
 
+/* Device memory a loop with this description would hold once created
+ * (resident_bytes) and at most during creation (peak_bytes, with the upload
+ * buffers), computed from the description alone without touching the GPU;
+ * this is what admission by HBM footprint uses.  Validation as rtc_create. */
+int rtc_footprint(const rtc_geometry* geometry, const rtc_calib* calib, const rtc_cmat* cmat,
+                  const rtc_polc* polc, uint64_t* resident_bytes, uint64_t* peak_bytes);
+
 /* Text of the last failure on this loop, or (loop NULL) of the last failed
  * rtc_create / stateless call on the calling thread.  Never NULL. */
 const char* rtc_last_error(const rtc_loop* loop);
@@ -313,6 +336,53 @@ const char* rtc_last_error(const rtc_loop* loop);
  * default stream).  Asynchronous; returns RTC_EINVAL on bad arguments. */
 int rtc_quantize_rows(int32_t dtype, int32_t na, int32_t ns, const float* M, size_t ld,
                       void* codes, float* scale, void* stream);
+
+/* ---- multi-loop server ---------------------------------------------------- */
+
+/* Several independent loops (SCAO, LTAO, MCAO ...) resident on one GPU, in the
+ * spirit of the paper's several DARC instances feeding one controller
+ * (Section 3), but whole loops sharing one device.  Loops are admitted by their
+ * device-memory footprint (rtc_footprint) against a budget; a loop that does
+ * not fit yet waits in a queue, with a private copy of its description, and is
+ * created when released loops free enough memory (arrival order).  Admitted
+ * loops run in graph mode (their flags gain RTC_FLAG_GRAPHS and lose
+ * RTC_FLAG_UPDATABLE and the timing flags): each frame is one CUDA graph
+ * launch on the loop's own stream, so frames of different loops overlap on
+ * the device.  A server thread polls the completion words and records, per
+ * loop, the latency from rtc_server_submit to the commands being written. */
+typedef struct rtc_server rtc_server;
+
+typedef struct rtc_server_loop_info {
+    int32_t admitted;          /* 1 resident on the device, 0 waiting in the queue */
+    uint64_t footprint_bytes;
+    uint64_t frames;           /* latency samples recorded (since the last reset) */
+    double p50_us, p99_us, p999_us, mean_us, jitter_rms_us, max_us;
+} rtc_server_loop_info;
+
+/* A server on device `device` with a device-memory budget in bytes. */
+int rtc_server_create(int32_t device, uint64_t hbm_budget_bytes, rtc_server** out);
+/* Stop the poller, destroy every loop, free the server.  NULL is accepted. */
+int rtc_server_destroy(rtc_server* server);
+/* Admit a loop (created now if it fits in the budget and nothing is queued
+ * ahead of it) or queue it; *loop_id names it either way.  RTC_ENOMEM if its
+ * footprint exceeds the whole budget; creation errors as rtc_create. */
+int rtc_server_admit(rtc_server* server, const rtc_geometry* geometry, const rtc_calib* calib,
+                     const rtc_cmat* cmat, const rtc_polc* polc, int32_t* loop_id);
+/* Destroy a loop (after its queued work) or drop it from the queue, then
+ * create queued loops that now fit. */
+int rtc_server_release(rtc_server* server, int32_t loop_id);
+/* The admitted loop's handle in *loop (NULL while queued), for
+ * rtc_next_frame_buffers, rtc_get_commands, rtc_get_telemetry and the state calls. */
+int rtc_server_loop(rtc_server* server, int32_t loop_id, rtc_loop** loop);
+/* Launch the loop's next frame graph (rtc_submit_frame_graph) and track its latency. */
+int rtc_server_submit(rtc_server* server, int32_t loop_id, uint64_t frame_id);
+/* Latency statistics and admission state of a loop; reset != 0 clears the samples. */
+int rtc_server_stats(rtc_server* server, int32_t loop_id, int32_t reset, rtc_server_loop_info* out);
+/* Bytes admitted against the budget, the budget, and loop counts. */
+int rtc_server_usage(rtc_server* server, uint64_t* used_bytes, uint64_t* budget_bytes, int32_t* admitted,
+                     int32_t* queued);
+/* Text of the server's last failure.  Never NULL. */
+const char* rtc_server_last_error(const rtc_server* server);
 
 /* ---- allocation-free reconstruction step ------------------------------ */
 

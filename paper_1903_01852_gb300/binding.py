@@ -22,7 +22,7 @@ RTC_EORDER, RTC_EDROPPED, RTC_ECUDA, RTC_ENOENT = -4, -5, -6, -7
 RTC_WFS_SH, RTC_WFS_PYRAMID = 0, 1
 RTC_F32, RTC_BF16, RTC_E4M3 = 0, 1, 2
 RTC_THRESH_SUBTRACT, RTC_THRESH_CLIP = 0, 1
-RTC_FLAG_TIMING, RTC_FLAG_TELEMETRY, RTC_FLAG_STAGE_TIMING, RTC_FLAG_UPDATABLE = 1, 2, 4, 8
+RTC_FLAG_TIMING, RTC_FLAG_TELEMETRY, RTC_FLAG_STAGE_TIMING, RTC_FLAG_UPDATABLE, RTC_FLAG_GRAPHS = 1, 2, 4, 8, 16
 RTC_MAX_WFS = 16
 DTYPES = {"f32": RTC_F32, "bf16": RTC_BF16, "e4m3": RTC_E4M3}
 CODE_NP = {RTC_F32: np.float32, RTC_BF16: np.uint16, RTC_E4M3: np.uint8}
@@ -78,6 +78,12 @@ class rtc_update_desc(C.Structure):
                 ("amin", C.c_float), ("amax", C.c_float)]
 
 
+class rtc_server_loop_info(C.Structure):
+    _fields_ = [("admitted", C.c_int32), ("footprint_bytes", C.c_uint64), ("frames", C.c_uint64),
+                ("p50_us", C.c_double), ("p99_us", C.c_double), ("p999_us", C.c_double), ("mean_us", C.c_double),
+                ("jitter_rms_us", C.c_double), ("max_us", C.c_double)]
+
+
 class rtc_info(C.Structure):
     _fields_ = [("na", C.c_int32), ("ns", C.c_int32), ("nwfs", C.c_int32), ("nblocks", C.c_int32),
                 ("nrows", C.c_int32), ("m_dtype", C.c_int32), ("p_dtype", C.c_int32),
@@ -93,6 +99,8 @@ SIGNATURES = [
     ("rtc_destroy", C.c_int, [C.c_void_p]),
     ("rtc_submit_pixels", C.c_int, [C.c_void_p, C.POINTER(rtc_chunk)]),
     ("rtc_process_frame", C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(C.c_void_p), C.POINTER(C.c_size_t)]),
+    ("rtc_next_frame_buffers", C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_size_t)]),
+    ("rtc_submit_frame_graph", C.c_int, [C.c_void_p, C.c_uint64]),
     ("rtc_get_commands", C.c_int, [C.c_void_p, f32p, C.c_size_t, C.POINTER(C.c_uint64), C.c_int64]),
     ("rtc_get_telemetry", C.c_int, [C.c_void_p, C.c_uint64, f32p, C.c_size_t, f32p, C.c_size_t, C.c_int64]),
     ("rtc_get_timing", C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(rtc_timing), C.c_int64]),
@@ -102,7 +110,20 @@ SIGNATURES = [
     ("rtc_sync", C.c_int, [C.c_void_p]),
     ("rtc_get_stream", C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
     ("rtc_get_info", C.c_int, [C.c_void_p, C.POINTER(rtc_info)]),
+    ("rtc_footprint", C.c_int, [C.POINTER(rtc_geometry), C.POINTER(rtc_calib), C.POINTER(rtc_cmat),
+                                C.POINTER(rtc_polc), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     ("rtc_last_error", C.c_char_p, [C.c_void_p]),
+    ("rtc_server_create", C.c_int, [C.c_int32, C.c_uint64, C.POINTER(C.c_void_p)]),
+    ("rtc_server_destroy", C.c_int, [C.c_void_p]),
+    ("rtc_server_admit", C.c_int, [C.c_void_p, C.POINTER(rtc_geometry), C.POINTER(rtc_calib), C.POINTER(rtc_cmat),
+                                   C.POINTER(rtc_polc), C.POINTER(C.c_int32)]),
+    ("rtc_server_release", C.c_int, [C.c_void_p, C.c_int32]),
+    ("rtc_server_loop", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]),
+    ("rtc_server_submit", C.c_int, [C.c_void_p, C.c_int32, C.c_uint64]),
+    ("rtc_server_stats", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(rtc_server_loop_info)]),
+    ("rtc_server_usage", C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(C.c_int32),
+                                   C.POINTER(C.c_int32)]),
+    ("rtc_server_last_error", C.c_char_p, [C.c_void_p]),
     ("rtc_quantize_rows", C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_size_t, C.c_void_p,
                                     C.c_void_p, C.c_void_p]),
     ("rtc_reconstruct_noalloc", C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p,
@@ -162,69 +183,96 @@ def _pitch(x):
     return x.strides[0]
 
 
+class _Described:
+    """The C structs of one loop description, and the arrays they point into."""
+
+
+def describe(cfg, device=0, flags=0, ring=4):
+    """Build rtc_geometry / rtc_calib / rtc_cmat / rtc_polc from a configuration dict."""
+    wl = cfg["wfs"]
+    if len(wl) > RTC_MAX_WFS:
+        raise ValueError("too many WFS")
+    st = _Described()
+    keep = []   # host arrays that must outlive the call that uses the structs
+    warr = (rtc_wfs * len(wl))()
+    darks = (f32p * len(wl))()
+    flats = (f32p * len(wl))()
+    thr = np.array([w.get("threshold", 0.0) for w in wl], np.float32)
+    mode = np.array([RTC_THRESH_CLIP if w.get("thresh_mode") == "clip" else RTC_THRESH_SUBTRACT for w in wl],
+                    np.int32)
+    for k, w in enumerate(wl):
+        s = warr[k]
+        s.kind = RTC_WFS_SH if w["kind"] == "sh" else RTC_WFS_PYRAMID
+        s.width, s.height = w["width"], w["height"]
+        if w["kind"] == "sh":
+            s.nsubx, s.nsuby, s.npx, s.ox, s.oy = w["nsubx"], w["nsuby"], w["npx"], w["ox"], w["oy"]
+        else:
+            s.pupil = w["pupil"]
+            for q in range(4):
+                s.qx[q], s.qy[q] = w["qx"][q], w["qy"][q]
+        v = np.ascontiguousarray(w["valid"], dtype=np.uint8)
+        keep.append(v)
+        s.valid = v.ctypes.data_as(C.POINTER(C.c_uint8))
+        s.nblocks = int(w.get("nblocks", 1))
+        d, f = _f32(w.get("dark")), _f32(w.get("flat"))
+        keep += [d, f]
+        darks[k] = _fptr(d)
+        flats[k] = _fptr(f)
+    st.geo = rtc_geometry(len(wl), warr, device, flags, ring)
+    ref = _f32(cfg.get("ref_slopes"))
+    st.cal = rtc_calib(darks, flats, thr.ctypes.data_as(f32p), mode.ctypes.data_as(C.POINTER(C.c_int32)), _fptr(ref))
+    mdt = DTYPES[cfg.get("M_dtype", "f32")]
+    M = np.ascontiguousarray(cfg["M"], dtype=CODE_NP[mdt])
+    ms = _f32(cfg.get("M_scale"))
+    st.cm = rtc_cmat(M.shape[0], M.shape[1], mdt, M.ctypes.data, _fptr(ms))
+    P = cfg.get("P")
+    pdt = DTYPES[cfg.get("P_dtype", "f32")]
+    Pa = None if P is None else np.ascontiguousarray(P, dtype=CODE_NP[pdt])
+    ps = _f32(cfg.get("P_scale"))
+    a0 = _f32(cfg.get("a0"))
+    clip = cfg.get("clip")
+    st.pol = rtc_polc(None if Pa is None else Pa.ctypes.data, pdt, _fptr(ps), float(cfg["gain"]), float(cfg["leak"]),
+                      _fptr(a0), 1 if clip else 0, float(clip[0]) if clip else 0.0, float(clip[1]) if clip else 0.0)
+    st.keep = keep + [warr, darks, flats, thr, mode, ref, M, ms, Pa, ps, a0]
+    return st
+
+
+def footprint(cfg, flags=0):
+    """rtc_footprint: (resident, peak) device bytes of a loop built from cfg."""
+    st = describe(cfg, 0, flags)
+    r, p = C.c_uint64(), C.c_uint64()
+    _check(lib.rtc_footprint(C.byref(st.geo), C.byref(st.cal), C.byref(st.cm), C.byref(st.pol), C.byref(r),
+                             C.byref(p)))
+    return r.value, p.value
+
+
 class Loop:
     """One AO loop on one GPU, built from a configuration dict (see synth)."""
 
-    def __init__(self, cfg, device=0, timing=False, telemetry=False, ring=4, stage_timing=False, updatable=False):
+    def __init__(self, cfg, device=0, timing=False, telemetry=False, ring=4, stage_timing=False, updatable=False,
+                 graphs=False, _handle=None):
         self.cfg = cfg
         self.na = int(cfg["na"])
-        wl = cfg["wfs"]
-        if len(wl) > RTC_MAX_WFS:
-            raise ValueError("too many WFS")
-        keep = []   # host arrays that must outlive rtc_create
-        warr = (rtc_wfs * len(wl))()
-        darks = (f32p * len(wl))()
-        flats = (f32p * len(wl))()
-        thr = np.array([w.get("threshold", 0.0) for w in wl], np.float32)
-        mode = np.array([RTC_THRESH_CLIP if w.get("thresh_mode") == "clip" else RTC_THRESH_SUBTRACT for w in wl],
-                        np.int32)
-        for k, w in enumerate(wl):
-            s = warr[k]
-            s.kind = RTC_WFS_SH if w["kind"] == "sh" else RTC_WFS_PYRAMID
-            s.width, s.height = w["width"], w["height"]
-            if w["kind"] == "sh":
-                s.nsubx, s.nsuby, s.npx, s.ox, s.oy = w["nsubx"], w["nsuby"], w["npx"], w["ox"], w["oy"]
-            else:
-                s.pupil = w["pupil"]
-                for q in range(4):
-                    s.qx[q], s.qy[q] = w["qx"][q], w["qy"][q]
-            v = np.ascontiguousarray(w["valid"], dtype=np.uint8)
-            keep.append(v)
-            s.valid = v.ctypes.data_as(C.POINTER(C.c_uint8))
-            s.nblocks = int(w.get("nblocks", 1))
-            d, f = _f32(w.get("dark")), _f32(w.get("flat"))
-            keep += [d, f]
-            darks[k] = _fptr(d)
-            flats[k] = _fptr(f)
-        flags = ((RTC_FLAG_TIMING if timing or stage_timing else 0) | (RTC_FLAG_TELEMETRY if telemetry else 0)
-                 | (RTC_FLAG_STAGE_TIMING if stage_timing else 0) | (RTC_FLAG_UPDATABLE if updatable else 0))
-        geo = rtc_geometry(len(wl), warr, device, flags, ring)
-        ref = _f32(cfg.get("ref_slopes"))
-        cal = rtc_calib(darks, flats, thr.ctypes.data_as(f32p), mode.ctypes.data_as(C.POINTER(C.c_int32)), _fptr(ref))
-        mdt = DTYPES[cfg.get("M_dtype", "f32")]
-        M = np.ascontiguousarray(cfg["M"], dtype=CODE_NP[mdt])
-        ms = _f32(cfg.get("M_scale"))
-        cm = rtc_cmat(M.shape[0], M.shape[1], mdt, M.ctypes.data, _fptr(ms))
-        P = cfg.get("P")
-        pdt = DTYPES[cfg.get("P_dtype", "f32")]
-        Pa = None if P is None else np.ascontiguousarray(P, dtype=CODE_NP[pdt])
-        ps = _f32(cfg.get("P_scale"))
-        a0 = _f32(cfg.get("a0"))
-        clip = cfg.get("clip")
-        pol = rtc_polc(None if Pa is None else Pa.ctypes.data, pdt, _fptr(ps), float(cfg["gain"]), float(cfg["leak"]),
-                       _fptr(a0), 1 if clip else 0, float(clip[0]) if clip else 0.0, float(clip[1]) if clip else 0.0)
-        h = C.c_void_p()
-        _check(lib.rtc_create(C.byref(geo), C.byref(cal), C.byref(cm), C.byref(pol), C.byref(h)))
-        self._h = h
+        self._owned = _handle is None
+        if _handle is None:
+            flags = ((RTC_FLAG_TIMING if timing or stage_timing else 0) | (RTC_FLAG_TELEMETRY if telemetry else 0)
+                     | (RTC_FLAG_STAGE_TIMING if stage_timing else 0) | (RTC_FLAG_UPDATABLE if updatable else 0)
+                     | (RTC_FLAG_GRAPHS if graphs else 0))
+            st = describe(cfg, device, flags, ring)
+            h = C.c_void_p()
+            _check(lib.rtc_create(C.byref(st.geo), C.byref(st.cal), C.byref(st.cm), C.byref(st.pol), C.byref(h)))
+            self._h = h
+        else:
+            self._h = C.c_void_p(_handle)
         inf = self.info()
         self.ns = inf["ns"]
         self._cmd = np.empty(self.na, np.float32)
 
     # -- lifetime ---------------------------------------------------------
     def close(self):
-        if getattr(self, "_h", None) and self._h.value:
+        if getattr(self, "_h", None) and self._h.value and getattr(self, "_owned", True):
             lib.rtc_destroy(self._h)
-            self._h = C.c_void_p()
+        self._h = C.c_void_p()
 
     def __enter__(self):
         return self
@@ -266,6 +314,23 @@ class Loop:
         px = (C.c_void_p * n)(*[t.data_ptr() for t in dev_frames])
         pitch = (C.c_size_t * n)(*[t.stride(0) * t.element_size() for t in dev_frames])
         return _check(lib.rtc_process_frame(self._h, frame_id, px, pitch), self._h, allow=(RTC_EDROPPED,))
+
+    def next_frame_buffers(self):
+        """Graph mode: numpy views (uint16, height x width) of the page-locked buffers the
+        next frame is written into."""
+        n = len(self.cfg["wfs"])
+        px = (C.c_void_p * n)()
+        pitch = (C.c_size_t * n)()
+        _check(lib.rtc_next_frame_buffers(self._h, px, pitch), self._h)
+        out = []
+        for k, w in enumerate(self.cfg["wfs"]):
+            buf = (C.c_uint16 * (w["height"] * pitch[k] // 2)).from_address(px[k])
+            out.append(np.frombuffer(buf, dtype=np.uint16).reshape(w["height"], pitch[k] // 2)[:, :w["width"]])
+        return out
+
+    def submit_graph(self, frame_id):
+        """Graph mode: launch the captured frame graph on the buffers last returned."""
+        return _check(lib.rtc_submit_frame_graph(self._h, frame_id), self._h, allow=(RTC_EDROPPED,))
 
     def get_commands(self, timeout_us=-1, out=None):
         out = self._cmd.copy() if out is None else out
@@ -367,3 +432,75 @@ def quantize_rows(M, fmt, stream=None):
     st = stream if stream is not None else torch.cuda.current_stream(M.device).cuda_stream
     _check(lib.rtc_quantize_rows(dt, na, ns, M.data_ptr(), M.stride(0), codes.data_ptr(), scale.data_ptr(), st))
     return codes, scale
+
+
+class Server:
+    """Several loops resident on one GPU, admitted by device-memory footprint (rtc_server_*)."""
+
+    def __init__(self, budget_bytes, device=0):
+        h = C.c_void_p()
+        _check(lib.rtc_server_create(device, int(budget_bytes), C.byref(h)))
+        self._h = h
+        self.cfgs = {}
+
+    def _err(self):
+        return lib.rtc_server_last_error(self._h).decode(errors="replace")
+
+    def admit(self, cfg, telemetry=False, ring=4):
+        st = describe(cfg, 0, RTC_FLAG_TELEMETRY if telemetry else 0, ring)
+        lid = C.c_int32()
+        rc = lib.rtc_server_admit(self._h, C.byref(st.geo), C.byref(st.cal), C.byref(st.cm), C.byref(st.pol),
+                                  C.byref(lid))
+        if rc != RTC_OK:
+            raise RtcError(rc, self._err())
+        self.cfgs[lid.value] = cfg
+        return lid.value
+
+    def loop(self, lid):
+        """A non-owning Loop view of an admitted loop (None while queued)."""
+        h = C.c_void_p()
+        rc = lib.rtc_server_loop(self._h, lid, C.byref(h))
+        if rc != RTC_OK:
+            raise RtcError(rc, self._err())
+        return None if not h.value else Loop(self.cfgs[lid], _handle=h.value)
+
+    def submit(self, lid, frame_id):
+        rc = lib.rtc_server_submit(self._h, lid, frame_id)
+        if rc not in (RTC_OK, RTC_EDROPPED):
+            raise RtcError(rc, self._err())
+        return rc
+
+    def stats(self, lid, reset=False):
+        i = rtc_server_loop_info()
+        rc = lib.rtc_server_stats(self._h, lid, 1 if reset else 0, C.byref(i))
+        if rc != RTC_OK:
+            raise RtcError(rc, self._err())
+        return {k: getattr(i, k) for k, _ in rtc_server_loop_info._fields_}
+
+    def usage(self):
+        u, b, a, q = C.c_uint64(), C.c_uint64(), C.c_int32(), C.c_int32()
+        _check(lib.rtc_server_usage(self._h, C.byref(u), C.byref(b), C.byref(a), C.byref(q)))
+        return dict(used=u.value, budget=b.value, admitted=a.value, queued=q.value)
+
+    def release(self, lid):
+        rc = lib.rtc_server_release(self._h, lid)
+        if rc != RTC_OK:
+            raise RtcError(rc, self._err())
+        self.cfgs.pop(lid, None)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib.rtc_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

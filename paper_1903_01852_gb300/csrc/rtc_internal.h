@@ -63,7 +63,8 @@ struct FinaliseArgs {
     float amin, amax;
     unsigned* tiles_done;     // tiles finalised this frame
     unsigned long long* done_flag;  // page-locked completion word of the ring slot, or NULL
-    unsigned long long seq;   // value written to done_flag once every tile is final
+    const unsigned long long* seq;  // page-locked word holding the value to write there (set by the
+                                    // host before the launch, so a captured graph can be replayed)
 };
 
 // Frame pointers for one launch; pitch in uint16 elements.  px[w] holds pixel
@@ -120,5 +121,11 @@ cudaError_t launch_quantize(int dtype, int na, int ns, const float* M, size_t ld
 
 // Finite check of a device float array; sets *bad (device int) to 1 if a NaN/Inf is found.
 cudaError_t launch_check_finite(const float* x, size_t n, int* bad, cudaStream_t st);
+
+// Loop internals used by the multi-loop server (implemented in rtc_runtime.cu).
+// The ring slot and completion value of the frame submitted last.
+void loop_last_frame(const rtc_loop* L, int* slot, unsigned long long* seq);
+// Whether that frame's commands are written (reads its page-locked completion word).
+bool loop_frame_done(const rtc_loop* L, int slot, unsigned long long seq);
 
 }  // namespace rtc

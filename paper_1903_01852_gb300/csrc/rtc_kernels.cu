@@ -483,7 +483,8 @@ __global__ void __launch_bounds__(kGemvWarps * 32) gemv_kernel(const __grid_cons
             if (atomicAdd(a.fin.tiles_done, 1u) == (unsigned)(nfin - 1)) {
                 *a.fin.tiles_done = 0u;
                 __threadfence_system();
-                *reinterpret_cast<volatile unsigned long long*>(a.fin.done_flag) = a.fin.seq;
+                const unsigned long long seq = *reinterpret_cast<const volatile unsigned long long*>(a.fin.seq);
+                *reinterpret_cast<volatile unsigned long long*>(a.fin.done_flag) = seq;
             }
         }
     }

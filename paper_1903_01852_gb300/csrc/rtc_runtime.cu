@@ -88,6 +88,8 @@ struct rtc_loop {
     float* d_ring = nullptr;
     unsigned long long* h_done = nullptr;   // page-locked completion words, one per slot
     unsigned long long* d_done = nullptr;
+    unsigned long long* h_seq = nullptr;    // per slot: the value its frame writes to h_done (host-set)
+    unsigned long long* d_seq = nullptr;
     unsigned* d_tiles_done = nullptr;
     uint64_t frame_seq = 0;
     size_t slot_floats = 0;
@@ -137,11 +139,22 @@ struct rtc_loop {
     std::string err;
     bool broken = false;
     bool cuda_touched = false;   // false until creation first calls into CUDA
+    bool plan_only = false;      // rtc_footprint: stop after planning, before any CUDA call
+    uint64_t need_resident = 0, need_peak = 0;
+
+    // graph mode (RTC_FLAG_GRAPHS): per ring slot, page-locked input frames and a captured frame graph
+    bool graphs = false;
+    std::vector<std::vector<uint16_t*>> g_px;    // [slot][wfs] page-locked frame (host address = device address)
+    std::vector<size_t> g_pitch;                 // [wfs] bytes
+    std::vector<cudaGraphExec_t> g_exec;         // [slot]
+    bool capturing = false;
 };
 
 namespace {
 
 enum : unsigned { kUpdM = 1u, kUpdMscale = 2u, kUpdP = 4u, kUpdPscale = 8u, kUpdTable = 16u, kUpdRef = 32u };
+
+int capture_graphs(rtc_loop* L);
 
 int fail(rtc_loop* L, int code, const std::string& msg) {
     if (L) L->err = msg;
@@ -208,6 +221,11 @@ void release(rtc_loop* L) {
     for (auto& s : L->slots)
         for (cudaEvent_t e : {s.ev_start, s.ev_tail, s.ev_slopes, s.ev_mvm, s.ev_final, s.ev_polc, s.ev_tel})
             if (e) cudaEventDestroy(e);
+    for (cudaGraphExec_t g : L->g_exec)
+        if (g) cudaGraphExecDestroy(g);
+    for (auto& v : L->g_px)
+        for (uint16_t* p : v)
+            if (p) cudaFreeHost(p);
     for (void* p : L->allocs) cudaFree(p);
     if (L->h_ring) cudaFreeHost(L->h_ring);
     if (L->h_done) cudaFreeHost(L->h_done);
@@ -308,13 +326,8 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
     L->clip = P->clip;
     L->amin = P->amin;
     L->amax = P->amax;
-    L->cuda_touched = true;
-    int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || L->dev < 0 || L->dev >= ndev) {
-        cudaGetLastError();
-        return fail(L, RTC_EINVAL, "no such CUDA device");
-    }
-    CK(L, cudaSetDevice(L->dev));
+    L->graphs = (G->flags & RTC_FLAG_GRAPHS) != 0;
+    if (L->graphs && L->updatable) return fail(L, RTC_EINVAL, "RTC_FLAG_GRAPHS and RTC_FLAG_UPDATABLE exclude each other");
 
     // ---- slope-row and block plans ------------------------------------
     const int V = elems_per_16B(L->m_dtype);
@@ -464,6 +477,19 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
         if (L->has_polc) need += (size_t)L->na * round_up(L->na, VP) * dtype_size(L->p_dtype);
         for (auto& w : L->wfs) need += (size_t)w.height * round_up(w.width, 4) * 8;
     }
+    const size_t temporary = (size_t)L->na * M->ns * dtype_size(L->m_dtype) +
+                             (L->has_polc ? (size_t)L->na * round_up(L->na, VP) * dtype_size(L->p_dtype) : 0);
+    L->need_peak = need;
+    L->need_resident = need - temporary;
+    if (L->plan_only) return RTC_OK;
+
+    L->cuda_touched = true;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || L->dev < 0 || L->dev >= ndev) {
+        cudaGetLastError();
+        return fail(L, RTC_EINVAL, "no such CUDA device");
+    }
+    CK(L, cudaSetDevice(L->dev));
     size_t free_b = 0, total_b = 0;
     CK(L, cudaMemGetInfo(&free_b, &total_b));
     if (need + (64u << 20) > free_b)
@@ -608,16 +634,18 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
     }
     {
         void* h = nullptr;
-        cudaError_t e = cudaHostAlloc(&h, (size_t)L->ring * sizeof(unsigned long long), cudaHostAllocMapped);
+        cudaError_t e = cudaHostAlloc(&h, 2 * (size_t)L->ring * sizeof(unsigned long long), cudaHostAllocMapped);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return fail(L, RTC_ENOMEM, "page-locked completion words");
         }
         L->h_done = static_cast<unsigned long long*>(h);
-        std::memset(h, 0, (size_t)L->ring * sizeof(unsigned long long));
+        L->h_seq = L->h_done + L->ring;
+        std::memset(h, 0, 2 * (size_t)L->ring * sizeof(unsigned long long));
         void* d = nullptr;
         CK(L, cudaHostGetDevicePointer(&d, h, 0));
         L->d_done = static_cast<unsigned long long*>(d);
+        L->d_seq = L->d_done + L->ring;
     }
     TRY(dev_alloc(L, &L->d_tiles_done, sizeof(unsigned)));
     CK(L, cudaMemset(L->d_tiles_done, 0, sizeof(unsigned)));
@@ -638,6 +666,7 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
     L->rows_done.assign(L->nwfs, 0);
     L->blks_done.assign(L->nwfs, 0);
     CK(L, cudaStreamSynchronize(L->st));
+    if (L->graphs) TRY(capture_graphs(L));
     return RTC_OK;
 }
 
@@ -680,11 +709,16 @@ int apply_pending_update(rtc_loop* L) {
     return RTC_OK;
 }
 
-// Start a frame: pick its ring slot (discarding an unread frame that still holds it).
-void begin_frame(rtc_loop* L, uint64_t id, bool chunked) {
+// Start a frame: pick its ring slot (discarding an unread frame that still holds it,
+// and waiting for the GPU to finish a frame that still uses it).
+int begin_frame(rtc_loop* L, uint64_t id, bool chunked) {
     L->active = chunked;
     L->cur_id = id;
     L->cur_slot = (int)(L->seq % (uint64_t)L->ring);
+    {
+        Slot& prev = L->slots[L->cur_slot];
+        if (prev.seq && L->h_done[L->cur_slot] != prev.seq) CK(L, cudaEventSynchronize(prev.ev_polc));
+    }
     {
         std::lock_guard<std::mutex> g(L->mu);
         auto it = std::find(L->pending.begin(), L->pending.end(), L->cur_slot);
@@ -697,32 +731,47 @@ void begin_frame(rtc_loop* L, uint64_t id, bool chunked) {
         s.frame_id = id;
         s.chunked = chunked;
         s.seq = ++L->frame_seq;
+        L->h_seq[L->cur_slot] = s.seq;
     }
     std::fill(L->rows_in.begin(), L->rows_in.end(), 0);
     std::fill(L->rows_done.begin(), L->rows_done.end(), 0);
     std::fill(L->blks_done.begin(), L->blks_done.end(), 0);
     L->tail_recorded = false;
+    return RTC_OK;
 }
 
-// After the MVM (whose tail wrote the commands): POLC for the next frame,
-// telemetry, then publish the slot.
-int finish_frame(rtc_loop* L) {
+// Event record.  Inside a stream capture it only marks a fork/join point of the
+// graph; graph launches record the slot's events again after the launch.
+int record(rtc_loop* L, cudaEvent_t e, cudaStream_t st) {
+    CK(L, cudaEventRecord(e, st));
+    return RTC_OK;
+}
+
+// After the MVM (whose tail wrote the commands): POLC for the next frame and the
+// telemetry copy.  Stream work only, so it can also be captured into a graph.
+int enqueue_tail(rtc_loop* L) {
     Slot& s = L->slots[L->cur_slot];
     float* cmd = L->d_ring + (size_t)L->cur_slot * L->slot_floats;
-    if (L->timing) CK(L, cudaEventRecord(s.ev_final, L->st));
+    if (L->timing) TRY(record(L, s.ev_final, L->st));
     if (L->has_polc)
         CK(L, launch_gemv(L->p_dtype, L->d_P, L->d_pblock, 0, 1, L->na, L->d_a, L->d_Pscale, L->d_q, 0, nullptr,
                           (long long)(L->p_bytes / std::max(L->na, 1)), !L->timing, L->st));
-    CK(L, cudaEventRecord(s.ev_polc, L->st));
+    TRY(record(L, s.ev_polc, L->st));
     if (L->telemetry) {
         CK(L, cudaStreamWaitEvent(L->st_tel, s.ev_polc, 0));
         CK(L, launch_pack_slopes(L->d_blocks, L->nblk, std::max(L->max_cols, 1), L->d_s,
                                  cmd + round_up((size_t)L->na, 4), L->st_tel));
-        CK(L, cudaEventRecord(s.ev_tel, L->st_tel));
+        TRY(record(L, s.ev_tel, L->st_tel));
         CK(L, cudaStreamWaitEvent(L->st, s.ev_tel, 0));   // the next frame rewrites the slopes
     } else {
-        CK(L, cudaEventRecord(s.ev_tel, L->st));
+        TRY(record(L, s.ev_tel, L->st));
     }
+    return RTC_OK;
+}
+
+// Host bookkeeping once a frame's work is enqueued: publish its slot to readers.
+int publish_frame(rtc_loop* L) {
+    Slot& s = L->slots[L->cur_slot];
     {
         std::lock_guard<std::mutex> g(L->mu);
         s.used = true;
@@ -735,6 +784,11 @@ int finish_frame(rtc_loop* L) {
     L->last_id = L->cur_id;
     ++L->seq;
     return RTC_OK;
+}
+
+int finish_frame(rtc_loop* L) {
+    TRY(enqueue_tail(L));
+    return publish_frame(L);
 }
 
 FinaliseArgs fin_args(rtc_loop* L) {
@@ -753,7 +807,7 @@ FinaliseArgs fin_args(rtc_loop* L) {
     f.amax = L->amax;
     f.tiles_done = L->d_tiles_done;
     f.done_flag = L->d_done + L->cur_slot;
-    f.seq = L->slots[L->cur_slot].seq;
+    f.seq = L->d_seq + L->cur_slot;
     return f;
 }
 
@@ -818,7 +872,7 @@ int submit_impl(rtc_loop* L, const rtc_chunk* c) {
         if (L->have_last && c->frame_id <= L->last_id) return fail(L, RTC_EORDER, "frame id not increasing");
         if (c->row_begin != 0) return fail(L, RTC_EORDER, "a frame must start at row 0");
         TRY(apply_pending_update(L));
-        begin_frame(L, c->frame_id, true);
+        TRY(begin_frame(L, c->frame_id, true));
         if (L->timing) CK(L, cudaEventRecord(L->slots[L->cur_slot].ev_start, L->st));
     } else if (c->row_begin != L->rows_in[c->wfs]) {
         return fail(L, RTC_EORDER, "rows of a WFS must arrive in order without gaps");
@@ -884,6 +938,77 @@ int submit_impl(rtc_loop* L, const rtc_chunk* c) {
     return status;
 }
 
+// Stream work of one whole frame whose pixels are addressed by fp: slopes of
+// every row, the MVM (a programmatic dependent of the slope kernel) with its
+// fused finalisation, then the tail.  Shared by rtc_process_frame and the
+// captured frame graphs.
+int enqueue_whole_frame(rtc_loop* L, const FramePtrs& fp) {
+    Slot& s = L->slots[L->cur_slot];
+    if (L->timing) {
+        TRY(record(L, s.ev_start, L->st));
+        TRY(record(L, s.ev_tail, L->st));
+    }
+    TRY(slopes_rows(L, 0, L->nrows, fp));
+    if (L->stage_timing) TRY(record(L, s.ev_slopes, L->st));
+    const FinaliseArgs fa = fin_args(L);
+    CK(L, launch_gemv(L->m_dtype, L->d_M, L->d_blocks, 0, L->nblk, L->na, L->d_s, nullptr, L->d_part, L->na, &fa,
+                      avg_row_bytes(L), !L->stage_timing, L->st));
+    if (L->stage_timing) TRY(record(L, s.ev_mvm, L->st));
+    return enqueue_tail(L);
+}
+
+// Graph mode: one set of page-locked input frames per ring slot, and the whole
+// frame's stream work (slopes -> MVM -> POLC -> telemetry, with the
+// programmatic-launch edges) captured once per slot into a CUDA graph.
+int capture_graphs(rtc_loop* L) {
+    L->g_pitch.resize(L->nwfs);
+    for (int k = 0; k < L->nwfs; ++k) L->g_pitch[k] = round_up((size_t)L->wfs[k].width * 2, 16);
+    L->g_px.assign(L->ring, std::vector<uint16_t*>(L->nwfs, nullptr));
+    L->g_exec.assign(L->ring, nullptr);
+    for (int slot = 0; slot < L->ring; ++slot) {
+        FramePtrs fp{};
+        for (int k = 0; k < L->nwfs; ++k) {
+            void* h = nullptr;
+            const size_t bytes = (size_t)L->wfs[k].height * L->g_pitch[k];
+            if (cudaHostAlloc(&h, bytes, cudaHostAllocMapped) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(L, RTC_ENOMEM, "page-locked input frames");
+            }
+            std::memset(h, 0, bytes);
+            L->g_px[slot][k] = static_cast<uint16_t*>(h);
+            void* d = nullptr;
+            CK(L, cudaHostGetDevicePointer(&d, h, 0));
+            fp.px[k] = static_cast<const uint16_t*>(d);
+            fp.pitch[k] = (long long)(L->g_pitch[k] / 2);
+        }
+        L->cur_slot = slot;
+        L->capturing = true;
+        CK(L, cudaStreamBeginCapture(L->st, cudaStreamCaptureModeThreadLocal));
+        const int rc = enqueue_whole_frame(L, fp);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(L->st, &graph);
+        L->capturing = false;
+        if (rc != RTC_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(L, e, "cudaStreamEndCapture");
+        const cudaError_t ei = cudaGraphInstantiate(&L->g_exec[slot], graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) return cuda_fail(L, ei, "cudaGraphInstantiate");
+    }
+    L->cur_slot = 0;
+    return RTC_OK;
+}
+
+// The slot the next frame will use, once the GPU is done with its previous frame.
+int next_slot_free(rtc_loop* L, int* slot) {
+    *slot = (int)(L->seq % (uint64_t)L->ring);
+    const Slot& prev = L->slots[*slot];
+    if (prev.seq && L->h_done[*slot] != prev.seq) CK(L, cudaEventSynchronize(prev.ev_polc));
+    return RTC_OK;
+}
+
 int process_impl(rtc_loop* L, uint64_t id, const uint16_t* const* px, const size_t* pitch) {
     if (!px || !pitch) return fail(L, RTC_EINVAL, "px and pitch are required");
     FramePtrs fp{};
@@ -909,19 +1034,9 @@ int process_impl(rtc_loop* L, uint64_t id, const uint16_t* const* px, const size
         L->err = "frame " + std::to_string(L->cur_id) + " was incomplete and has been dropped";
     }
     TRY(apply_pending_update(L));
-    begin_frame(L, id, false);
-    Slot& s = L->slots[L->cur_slot];
-    if (L->timing) {
-        CK(L, cudaEventRecord(s.ev_start, L->st));
-        CK(L, cudaEventRecord(s.ev_tail, L->st));
-    }
-    TRY(slopes_rows(L, 0, L->nrows, fp));
-    if (L->stage_timing) CK(L, cudaEventRecord(s.ev_slopes, L->st));
-    const FinaliseArgs fa = fin_args(L);
-    CK(L, launch_gemv(L->m_dtype, L->d_M, L->d_blocks, 0, L->nblk, L->na, L->d_s, nullptr, L->d_part, L->na, &fa,
-                      avg_row_bytes(L), !L->stage_timing, L->st));
-    if (L->stage_timing) CK(L, cudaEventRecord(s.ev_mvm, L->st));
-    TRY(finish_frame(L));
+    TRY(begin_frame(L, id, false));
+    TRY(enqueue_whole_frame(L, fp));
+    TRY(publish_frame(L));
     return status;
 }
 
@@ -975,6 +1090,21 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
 
 }  // namespace
 
+namespace rtc {
+
+void loop_last_frame(const rtc_loop* L, int* slot, unsigned long long* seq) {
+    const int s = (int)((L->seq + (uint64_t)L->ring - 1) % (uint64_t)L->ring);
+    *slot = s;
+    *seq = L->slots[s].seq;
+}
+
+bool loop_frame_done(const rtc_loop* L, int slot, unsigned long long seq) {
+    const volatile unsigned long long* w = L->h_done + slot;
+    return *w == seq;
+}
+
+}  // namespace rtc
+
 extern "C" {
 
 int rtc_create(const rtc_geometry* geometry, const rtc_calib* calib, const rtc_cmat* cmat, const rtc_polc* polc,
@@ -1010,6 +1140,60 @@ int rtc_process_frame(rtc_loop* L, uint64_t frame_id, const uint16_t* const* px,
     if (L->broken) return fail(L, RTC_ECUDA, "loop is in a failed state: " + L->err);
     TRY(use_device(L));
     return process_impl(L, frame_id, px, pitch);
+}
+
+int rtc_next_frame_buffers(rtc_loop* L, uint16_t** px, size_t* pitch) {
+    if (!L || !px || !pitch) return fail(L, RTC_EINVAL, "loop, px and pitch are required");
+    if (!L->graphs) return fail(L, RTC_EINVAL, "loop created without RTC_FLAG_GRAPHS");
+    TRY(use_device(L));
+    int slot = 0;
+    TRY(next_slot_free(L, &slot));
+    for (int k = 0; k < L->nwfs; ++k) {
+        px[k] = L->g_px[slot][k];
+        pitch[k] = L->g_pitch[k];
+    }
+    return RTC_OK;
+}
+
+int rtc_submit_frame_graph(rtc_loop* L, uint64_t frame_id) {
+    if (!L) return fail(nullptr, RTC_EINVAL, "loop is NULL");
+    if (!L->graphs) return fail(L, RTC_EINVAL, "loop created without RTC_FLAG_GRAPHS");
+    if (L->broken) return fail(L, RTC_ECUDA, "loop is in a failed state: " + L->err);
+    TRY(use_device(L));
+    int status = RTC_OK;
+    if (L->active ? frame_id <= L->cur_id : (L->have_last && frame_id <= L->last_id))
+        return fail(L, RTC_EORDER, "frame id not increasing");
+    if (L->active) {
+        ++L->frames_dropped;
+        L->active = false;
+        TRY(reset_counters(L));
+        status = RTC_EDROPPED;
+    }
+    TRY(begin_frame(L, frame_id, false));
+    CK(L, cudaGraphLaunch(L->g_exec[L->cur_slot], L->st));
+    // the graph ends with the telemetry joined back into the loop's stream: these
+    // complete when the whole frame (POLC and telemetry included) has
+    Slot& s = L->slots[L->cur_slot];
+    CK(L, cudaEventRecord(s.ev_polc, L->st));
+    CK(L, cudaEventRecord(s.ev_tel, L->st));
+    TRY(publish_frame(L));
+    return status;
+}
+
+int rtc_footprint(const rtc_geometry* geometry, const rtc_calib* calib, const rtc_cmat* cmat, const rtc_polc* polc,
+                  uint64_t* resident_bytes, uint64_t* peak_bytes) {
+    rtc_loop* L = new (std::nothrow) rtc_loop();
+    if (!L) return fail(nullptr, RTC_ENOMEM, "host allocation failed");
+    L->plan_only = true;
+    const int rc = create_impl(geometry, calib, cmat, polc, L);
+    if (rc == RTC_OK) {
+        if (resident_bytes) *resident_bytes = L->need_resident;
+        if (peak_bytes) *peak_bytes = L->need_peak;
+    } else {
+        g_err = L->err.empty() ? g_err : L->err;
+    }
+    release(L);
+    return rc;
 }
 
 int rtc_get_commands(rtc_loop* L, float* out, size_t n, uint64_t* frame_id, int64_t timeout_us) {

@@ -56,3 +56,23 @@ def test_null_loop_calls_are_rejected(rtc):
     assert rtc.lib.rtc_submit_pixels(None, None) == rtc.RTC_EINVAL
     assert rtc.lib.rtc_destroy(None) == rtc.RTC_OK
     assert rtc.lib.rtc_last_error(None) is not None
+
+
+def test_footprint_is_computed_without_gpu_and_scales_with_storage(rtc):
+    import numpy as np
+    from paper_1903_01852_gb300 import synth
+    cfg = synth.make_config("elt_scao_sh")
+    r32, p32 = rtc.footprint(cfg)
+    q = dict(cfg, M=np.zeros(cfg["M"].shape, np.uint16), M_dtype="bf16",
+             M_scale=np.ones(cfg["na"], np.float32))
+    r16, p16 = rtc.footprint(q)
+    ru, _ = rtc.footprint(cfg, flags=rtc.RTC_FLAG_UPDATABLE)
+    matrix = cfg["na"] * cfg["ns"] * 4
+    assert r32 < p32 and r16 < p16
+    assert matrix <= r32 < matrix * 1.1
+    assert abs((r32 - r16) - matrix / 2) < 0.02 * matrix        # BF16 halves the matrix bytes
+    assert abs((ru - r32) - matrix) < 0.05 * matrix             # the double buffer adds one matrix
+    bad = dict(cfg, M=cfg["M"][:, :-2])
+    import pytest
+    with pytest.raises(rtc.RtcError):
+        rtc.footprint(bad)

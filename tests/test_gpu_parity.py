@@ -438,3 +438,94 @@ def test_update_while_frames_run_and_rejected_updates(rtc, torch_cuda):
         chk.set_state(state_before)
         chk.submit_frame(1, frames[fid % 2])
         assert np.array_equal(chk.get_commands(timeout_us=WAIT_US)[1], a_new)
+
+
+# ------------------------------------------------------------------ graphs and serving
+
+def write_frame(bufs, frame):
+    for b, f in zip(bufs, frame):
+        b[:] = f
+
+
+def wait_frames(srv, lid, n, timeout=5.0):
+    import time
+    t = time.time() + timeout
+    while srv.stats(lid)["frames"] < n and time.time() < t:
+        time.sleep(0.001)
+    return srv.stats(lid)["frames"]
+
+
+def test_graph_mode_equals_direct_launches_bitwise(rtc, torch_cuda):
+    cfg = synth.make_config("elt_scao_sh", polc=True, with_ref=True)
+    frames = synth.draw_frames(cfg, 6, seed=131)
+    ref = OracleLoop(cfg)
+    with rtc.Loop(cfg, telemetry=True, graphs=True, ring=3) as g, rtc.Loop(cfg, telemetry=True) as d:
+        for k, f in enumerate(frames):
+            write_frame(g.next_frame_buffers(), f)
+            g.submit_graph(k + 1)
+            d.process_frame(k + 1, device_frames(f))
+            fa, a = g.get_commands(timeout_us=WAIT_US)
+            fb, b = d.get_commands(timeout_us=WAIT_US)
+            assert fa == fb == k + 1 and np.array_equal(a, b)
+            s, _ = g.get_telemetry(fa, timeout_us=WAIT_US)
+            s_ref, a_ref = ref.step(f)
+            assert rel(s, s_ref) <= TOL_F32 and rel(a, a_ref) <= TOL_F32
+
+
+def test_server_admits_by_footprint_and_queues_until_memory_frees(rtc, torch_cuda):
+    a_cfg = synth.make_config("elt_scao_sh")
+    b_cfg = synth.make_config("elt_scao_pyramid")
+    fa = rtc.footprint(a_cfg, flags=rtc.RTC_FLAG_GRAPHS)[0]
+    fb = rtc.footprint(b_cfg, flags=rtc.RTC_FLAG_GRAPHS)[0]
+    frames = synth.draw_frames(b_cfg, 2, seed=132)
+    with rtc.Server(budget_bytes=max(fa, fb) + min(fa, fb) // 2) as srv:
+        ia = srv.admit(a_cfg)
+        ib = srv.admit(b_cfg)                       # does not fit next to A: queued
+        u = srv.usage()
+        assert u["admitted"] == 1 and u["queued"] == 1 and u["used"] == fa
+        assert srv.stats(ib)["admitted"] == 0 and srv.loop(ib) is None
+        with pytest.raises(rtc.RtcError):
+            srv.admit(dict(a_cfg, M=np.zeros((a_cfg["na"] * 3, a_cfg["ns"]), np.float32)))   # larger than the budget
+        srv.release(ia)                             # frees A's memory: B is created
+        u = srv.usage()
+        assert u["admitted"] == 1 and u["queued"] == 0 and u["used"] == fb
+        lb = srv.loop(ib)
+        ref = OracleLoop(b_cfg)
+        for k, f in enumerate(frames):
+            write_frame(lb.next_frame_buffers(), f)
+            srv.submit(ib, k + 1)
+            _, a = lb.get_commands(timeout_us=WAIT_US)
+            assert rel(a, ref.step(f)[1]) <= TOL_F32
+        assert wait_frames(srv, ib, 2) == 2
+
+
+def test_server_results_are_the_same_alone_and_in_the_mix(rtc, torch_cuda):
+    cfgs = [synth.make_config("scao_small"), ragged_config(seed=133), synth.make_config("elt_scao_sh", polc=True)]
+    frames = [synth.draw_frames(c, 5, seed=134 + i) for i, c in enumerate(cfgs)]
+    budget = sum(rtc.footprint(c, flags=rtc.RTC_FLAG_GRAPHS)[0] for c in cfgs) + (64 << 20)
+    alone = []
+    for c, fr in zip(cfgs, frames):
+        with rtc.Server(budget) as srv:
+            i = srv.admit(c)
+            lp = srv.loop(i)
+            out = []
+            for k, f in enumerate(fr):
+                write_frame(lp.next_frame_buffers(), f)
+                srv.submit(i, k + 1)
+                out.append(lp.get_commands(timeout_us=WAIT_US)[1])
+            alone.append(out)
+    with rtc.Server(budget) as srv:
+        ids = [srv.admit(c) for c in cfgs]
+        lps = [srv.loop(i) for i in ids]
+        mix = [[] for _ in cfgs]
+        for k in range(5):
+            # every loop's frame k is on the GPU at the same time, in a different order each round
+            order = [(k + j) % 3 for j in range(3)]
+            for j in order:
+                write_frame(lps[j].next_frame_buffers(), frames[j][k])
+                srv.submit(ids[j], k + 1)
+            for j in order:
+                mix[j].append(lps[j].get_commands(timeout_us=WAIT_US)[1])
+        for j in range(3):
+            assert all(np.array_equal(a, b) for a, b in zip(alone[j], mix[j])), j
+            assert wait_frames(srv, ids[j], 5) == 5
