@@ -560,6 +560,93 @@ def quick_arm(args, cfg, frames, rtc, torch, local):
                       "mvm_gbs": mvm_bytes(info, cfg) / (mvm * 1e-6) / 1e9}), flush=True)
 
 
+SERVING_LOOPS = (("ltao", "ltao", 500.0), ("mcao", "mcao", 500.0), ("scao_a", "elt_scao_sh", 1000.0),
+                 ("scao_b", "elt_scao_sh", 1000.0))
+
+
+def serving_arm(args):
+    """Serving mix on one GPU: a HARMONI-like LTAO loop, the MAORY-like MCAO loop and two ELT SCAO SH
+    loops resident at once (BF16 matrices, graph mode), admitted by HBM footprint into one server;
+    frames arrive at 500 Hz (LTAO, MCAO) and 1 kHz (SCAO) with seeded staggered phases and +-20 us
+    uniform jitter.  Latency per loop = rtc_server_submit -> commands written (the server's poller).
+    Each loop is also run alone with the same arrivals for comparison."""
+    import torch
+    from paper_1903_01852_gb300 import binding as rtc
+    from paper_1903_01852_gb300 import synth
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(4242)
+    cfgs, frames = {}, {}
+    for name, conf, _ in SERVING_LOOPS:
+        c = synth.make_config(conf, seed=5000 + len(cfgs))
+        cfgs[name] = quant_config(c, rtc, torch, "bf16")
+        frames[name] = synth.draw_frames(c, 2, seed=6000 + len(frames))
+    foot = {n: rtc.footprint(cfgs[n], flags=rtc.RTC_FLAG_GRAPHS)[0] for n in cfgs}
+    budget = int(sum(foot.values()) * 1.02)
+    dur = args.serving_seconds
+
+    def schedule(names):
+        ev = []
+        for n, _, hz in SERVING_LOOPS:
+            if n not in names:
+                continue
+            phase = rng.uniform(0, 1.0 / hz)
+            t = 0.02 + phase
+            while t < dur:
+                ev.append((t + rng.uniform(-20e-6, 20e-6), n))
+                t += 1.0 / hz
+        return sorted(ev)
+
+    def run(names):
+        with rtc.Server(budget) as srv:
+            ids = {n: srv.admit(cfgs[n]) for n in names}
+            lps = {n: srv.loop(ids[n]) for n in names}
+            for n in names:                       # stage two different frames in the ring's buffers
+                for k in range(2):
+                    for b, f in zip(lps[n].next_frame_buffers(), frames[n][k]):
+                        b[:] = f
+                    srv.submit(ids[n], k + 1)
+                    lps[n].get_commands(timeout_us=10_000_000)
+            for n in names:
+                srv.stats(ids[n], reset=True)
+            fid = {n: 10 for n in names}
+            ev = schedule(names)
+            gc.disable()
+            t0 = time.perf_counter()
+            for t, n in ev:
+                while time.perf_counter() - t0 < t:
+                    pass
+                lps[n].next_frame_buffers()      # the slot is free (its previous frame is done)
+                srv.submit(ids[n], fid[n])
+                fid[n] += 1
+                while True:                      # drain commands as they come (FIFO per loop)
+                    try:
+                        lps[n].get_commands(timeout_us=0)
+                    except TimeoutError:
+                        break
+            elapsed = time.perf_counter() - t0
+            gc.enable()
+            for n in names:
+                lps[n].sync()
+            time.sleep(0.05)
+            st = {n: srv.stats(ids[n]) for n in names}
+            usage = srv.usage()
+        return st, usage, len(ev) / elapsed
+
+    names = [n for n, _, _ in SERVING_LOOPS]
+    mix, usage, fps = run(names)
+    alone = {n: run([n])[0][n] for n in names}
+    keys = ("p50_us", "p99_us", "p999_us", "mean_us", "jitter_rms_us", "max_us", "frames")
+    out = {"mode": "serving", "metric": "per-loop frame latency, serving mix on one GB300 (BF16 matrices, graphs)",
+           "unit": "us", "seconds": dur, "frames_per_s": fps, "budget_bytes": budget,
+           "admitted_bytes": usage["used"], "footprint_bytes": foot,
+           "loops": {n: {"rate_hz": hz, "config": conf, "mix": {k: mix[n][k] for k in keys},
+                         "alone": {k: alone[n][k] for k in keys}} for n, conf, hz in SERVING_LOOPS},
+           "definition": "rtc_server_submit entry -> the loop's page-locked completion word set (server poller, "
+                         "host clock); arrivals at 500 Hz / 1 kHz, seeded phases, +-20 us jitter; 'alone' = the "
+                         "same loop and arrivals without the others"}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -571,6 +658,8 @@ def main():
     ap.add_argument("--paced-warmup", type=int, default=500)
     ap.add_argument("--parity-frames", type=int, default=20, help="frames checked against the FP64 oracle")
     ap.add_argument("--swap-frames", type=int, default=2500, help="paced frames of the parameter-swap run")
+    ap.add_argument("--serving", action="store_true", help="serving mix (LTAO + MCAO + 2 SCAO) instead")
+    ap.add_argument("--serving-seconds", type=float, default=4.0)
     ap.add_argument("--workload", default="mcao", help="configuration (profiling aid; the bench line is mcao)")
     ap.add_argument("--quick", action="store_true", help="profiling aid: only the unpaced loop")
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "e4m3"], help="matrix storage for --quick")
@@ -580,6 +669,9 @@ def main():
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         reference_arm(args, world, rank)
+    elif args.serving:
+        if rank == 0:
+            serving_arm(args)
     else:
         ours_arm(args, world, rank, local)
     if world > 1:
