@@ -96,6 +96,10 @@ struct rtc_loop {
     std::vector<Slot> slots;
 
     cudaStream_t st = nullptr, st_tel = nullptr;
+    // per WFS: the stream its chunks' work runs on (cameras overlap on the device), and its join event
+    std::vector<cudaStream_t> st_w;
+    std::vector<cudaEvent_t> ev_w;
+    cudaEvent_t ev_frame_end = nullptr;      // the loop stream's latest frame boundary
 
     // frame state (submitting thread)
     bool active = false;
@@ -105,7 +109,7 @@ struct rtc_loop {
     int cur_slot = 0;
     uint64_t seq = 0;
     std::vector<int> rows_in, rows_done, blks_done;
-    bool tail_recorded = false;
+    bool start_recorded = false;   // the frame's first chunk has recorded ev_start
 
     // completed-submission queue (shared with readers)
     std::mutex mu;
@@ -218,6 +222,13 @@ void release(rtc_loop* L) {
     if (cur != L->dev) cudaSetDevice(L->dev);
     if (L->st) cudaStreamSynchronize(L->st);
     if (L->st_tel) cudaStreamSynchronize(L->st_tel);
+    for (cudaStream_t w : L->st_w)
+        if (w) cudaStreamSynchronize(w);
+    for (cudaEvent_t e : L->ev_w)
+        if (e) cudaEventDestroy(e);
+    for (cudaStream_t w : L->st_w)
+        if (w) cudaStreamDestroy(w);
+    if (L->ev_frame_end) cudaEventDestroy(L->ev_frame_end);
     for (auto& s : L->slots)
         for (cudaEvent_t e : {s.ev_start, s.ev_tail, s.ev_slopes, s.ev_mvm, s.ev_final, s.ev_polc, s.ev_tel})
             if (e) cudaEventDestroy(e);
@@ -499,6 +510,13 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
     CK(L, configure_slopes(L->smem_bytes));
     CK(L, cudaStreamCreateWithPriority(&L->st, cudaStreamNonBlocking, -5));   // clamped to the highest priority
     CK(L, cudaStreamCreateWithFlags(&L->st_tel, cudaStreamNonBlocking));
+    L->st_w.assign(L->nwfs, nullptr);
+    L->ev_w.assign(L->nwfs, nullptr);
+    for (int k = 0; k < L->nwfs; ++k) {
+        CK(L, cudaStreamCreateWithPriority(&L->st_w[k], cudaStreamNonBlocking, -5));
+        CK(L, cudaEventCreateWithFlags(&L->ev_w[k], cudaEventDisableTiming));
+    }
+    CK(L, cudaEventCreateWithFlags(&L->ev_frame_end, cudaEventDisableTiming));
 
     // ---- device buffers ---------------------------------------------------
     TRY(dev_alloc(L, &L->d_blocks, L->blocks_h.size() * sizeof(BlockDev)));
@@ -736,7 +754,7 @@ int begin_frame(rtc_loop* L, uint64_t id, bool chunked) {
     std::fill(L->rows_in.begin(), L->rows_in.end(), 0);
     std::fill(L->rows_done.begin(), L->rows_done.end(), 0);
     std::fill(L->blks_done.begin(), L->blks_done.end(), 0);
-    L->tail_recorded = false;
+    L->start_recorded = false;
     return RTC_OK;
 }
 
@@ -765,6 +783,16 @@ int enqueue_tail(rtc_loop* L) {
         CK(L, cudaStreamWaitEvent(L->st, s.ev_tel, 0));   // the next frame rewrites the slopes
     } else {
         TRY(record(L, s.ev_tel, L->st));
+    }
+    if (!L->capturing) TRY(record(L, L->ev_frame_end, L->st));   // per-WFS streams start the next frame after it
+    return RTC_OK;
+}
+
+// Make the loop stream wait for the work every per-WFS stream has queued.
+int join_wfs_streams(rtc_loop* L) {
+    for (int k = 0; k < L->nwfs; ++k) {
+        CK(L, cudaEventRecord(L->ev_w[k], L->st_w[k]));
+        CK(L, cudaStreamWaitEvent(L->st, L->ev_w[k], 0));
     }
     return RTC_OK;
 }
@@ -811,10 +839,10 @@ FinaliseArgs fin_args(rtc_loop* L) {
     return f;
 }
 
-int slopes_rows(rtc_loop* L, int r0, int r1, const FramePtrs& fp) {
+int slopes_rows(rtc_loop* L, int r0, int r1, const FramePtrs& fp, cudaStream_t st) {
     const int p0 = L->part_start[r0], p1 = L->part_start[r1];
     CK(L, launch_slopes(L->d_parts, p0, p1 - p0, L->d_rows, L->d_wfs, fp, L->d_xlist, L->d_ref, L->d_s, L->d_pscr,
-                        L->d_row_cnt, L->smem_bytes, L->st));
+                        L->d_row_cnt, L->smem_bytes, st));
     return RTC_OK;
 }
 
@@ -822,9 +850,12 @@ long long avg_row_bytes(const rtc_loop* L) {
     return (long long)(L->m_bytes / ((uint64_t)std::max(L->na, 1) * std::max(L->nblk, 1)));
 }
 
-// A dropped frame may have counted some blocks of some row tiles: clear them.
+// A dropped frame may have counted some blocks of some row tiles: once all its
+// queued work is done, clear them; the next frame starts after that.
 int reset_counters(rtc_loop* L) {
+    TRY(join_wfs_streams(L));
     CK(L, cudaMemsetAsync(L->d_fin_cnt, 0, (size_t)L->nfin * sizeof(unsigned), L->st));
+    CK(L, cudaEventRecord(L->ev_frame_end, L->st));
     return RTC_OK;
 }
 
@@ -873,19 +904,24 @@ int submit_impl(rtc_loop* L, const rtc_chunk* c) {
         if (c->row_begin != 0) return fail(L, RTC_EORDER, "a frame must start at row 0");
         TRY(apply_pending_update(L));
         TRY(begin_frame(L, c->frame_id, true));
-        if (L->timing) CK(L, cudaEventRecord(L->slots[L->cur_slot].ev_start, L->st));
     } else if (c->row_begin != L->rows_in[c->wfs]) {
         return fail(L, RTC_EORDER, "rows of a WFS must arrive in order without gaps");
     }
     const int k = c->wfs;
     Slot& s = L->slots[L->cur_slot];
+    cudaStream_t sk = L->st_w[k];              // this camera's stream
+    if (L->rows_in[k] == 0) {                  // its first chunk of the frame: after the previous frame
+        CK(L, cudaStreamWaitEvent(sk, L->ev_frame_end, 0));
+        if (L->timing && !L->start_recorded) CK(L, cudaEventRecord(s.ev_start, sk));
+        L->start_recorded = true;
+    }
     // last chunk of the frame?
     bool last = true;
     for (int j = 0; j < L->nwfs; ++j) {
         const int got = j == k ? c->row_end : L->rows_in[j];
         if (got < L->wfs[j].height) last = false;
     }
-    if (last && L->timing) CK(L, cudaEventRecord(s.ev_tail, L->st));
+    if (last && L->timing) CK(L, cudaEventRecord(s.ev_tail, sk));
     // slope rows completed by these rows
     const int r0 = L->wfs_row0[k];
     const int done = L->rows_done[k];
@@ -912,14 +948,14 @@ int submit_impl(rtc_loop* L, const rtc_chunk* c) {
     }
     if (!in_place)
         CK(L, cudaMemcpy2DAsync(L->d_frame[k] + (size_t)c->row_begin * L->frame_pitch[k], L->frame_pitch[k] * 2, c->px,
-                                c->pitch, (size_t)w.width * 2, c->row_end - c->row_begin, cudaMemcpyDefault, L->st));
+                                c->pitch, (size_t)w.width * 2, c->row_end - c->row_begin, cudaMemcpyDefault, sk));
     L->rows_in[k] = c->row_end;
     const bool slopes_launched = upto > done;
     if (slopes_launched) {
-        TRY(slopes_rows(L, r0 + done, r0 + upto, fp));
+        TRY(slopes_rows(L, r0 + done, r0 + upto, fp, sk));
         L->rows_done[k] = upto;
     }
-    if (last && L->stage_timing) CK(L, cudaEventRecord(s.ev_slopes, L->st));
+    if (last && L->stage_timing) CK(L, cudaEventRecord(s.ev_slopes, sk));
     // column blocks completed by those slope rows
     const int b0 = L->wfs_blk0[k];
     int bd = L->blks_done[k];
@@ -928,11 +964,12 @@ int submit_impl(rtc_loop* L, const rtc_chunk* c) {
     if (bu > bd) {
         const FinaliseArgs fa = fin_args(L);
         CK(L, launch_gemv(L->m_dtype, L->d_M, L->d_blocks, b0 + bd, bu - bd, L->na, L->d_s, nullptr, L->d_part, L->na,
-                          &fa, avg_row_bytes(L), slopes_launched && !L->stage_timing, L->st));
+                          &fa, avg_row_bytes(L), slopes_launched && !L->stage_timing, sk));
         L->blks_done[k] = bu;
     }
     if (last) {
-        if (L->stage_timing) CK(L, cudaEventRecord(s.ev_mvm, L->st));
+        if (L->stage_timing) CK(L, cudaEventRecord(s.ev_mvm, sk));
+        TRY(join_wfs_streams(L));              // POLC and telemetry follow every camera's work
         TRY(finish_frame(L));
     }
     return status;
@@ -948,7 +985,7 @@ int enqueue_whole_frame(rtc_loop* L, const FramePtrs& fp) {
         TRY(record(L, s.ev_start, L->st));
         TRY(record(L, s.ev_tail, L->st));
     }
-    TRY(slopes_rows(L, 0, L->nrows, fp));
+    TRY(slopes_rows(L, 0, L->nrows, fp, L->st));
     if (L->stage_timing) TRY(record(L, s.ev_slopes, L->st));
     const FinaliseArgs fa = fin_args(L);
     CK(L, launch_gemv(L->m_dtype, L->d_M, L->d_blocks, 0, L->nblk, L->na, L->d_s, nullptr, L->d_part, L->na, &fa,
@@ -1176,6 +1213,7 @@ int rtc_submit_frame_graph(rtc_loop* L, uint64_t frame_id) {
     Slot& s = L->slots[L->cur_slot];
     CK(L, cudaEventRecord(s.ev_polc, L->st));
     CK(L, cudaEventRecord(s.ev_tel, L->st));
+    CK(L, cudaEventRecord(L->ev_frame_end, L->st));
     TRY(publish_frame(L));
     return status;
 }
@@ -1370,6 +1408,7 @@ int rtc_update(rtc_loop* L, const rtc_update_desc* d) {
 int rtc_get_state(rtc_loop* L, float* a, size_t na) {
     if (!L || !a || na != (size_t)L->na) return fail(L, RTC_EINVAL, "a must hold na floats");
     TRY(use_device(L));
+    for (cudaStream_t w : L->st_w) CK(L, cudaStreamSynchronize(w));
     CK(L, cudaStreamSynchronize(L->st));
     CK(L, cudaMemcpy(a, L->d_a, na * 4, cudaMemcpyDeviceToHost));
     return RTC_OK;
@@ -1379,6 +1418,7 @@ int rtc_set_state(rtc_loop* L, const float* a, size_t na) {
     if (!L || !a || na != (size_t)L->na) return fail(L, RTC_EINVAL, "a must hold na floats");
     if (!all_finite(a, na)) return fail(L, RTC_EINVAL, "state not finite");
     TRY(use_device(L));
+    for (cudaStream_t w : L->st_w) CK(L, cudaStreamSynchronize(w));
     CK(L, cudaStreamSynchronize(L->st));
     CK(L, cudaMemcpy(L->d_a, a, na * 4, cudaMemcpyHostToDevice));
     if (L->has_polc)
@@ -1390,6 +1430,7 @@ int rtc_set_state(rtc_loop* L, const float* a, size_t na) {
 int rtc_sync(rtc_loop* L) {
     if (!L) return fail(nullptr, RTC_EINVAL, "loop is NULL");
     TRY(use_device(L));
+    for (cudaStream_t w : L->st_w) CK(L, cudaStreamSynchronize(w));
     CK(L, cudaStreamSynchronize(L->st));
     CK(L, cudaStreamSynchronize(L->st_tel));
     return RTC_OK;
