@@ -534,6 +534,33 @@ def ours_arm(args, world, rank, local):
     print(json.dumps(res), flush=True)
 
 
+def format_errors(args, frames, rtc, dev_frames, local, nframes=10):
+    """Slope and command errors of the GPU loop against the FP64 oracle, per frame, for this
+    configuration and matrix format: against the oracle on the stored matrix (the parity check)
+    and against the oracle on the float32 matrix (the cost of the format)."""
+    import copy
+    from oracle import OracleLoop
+    from paper_1903_01852_gb300 import synth
+    base = synth.make_config(args.workload)
+    cfg = quant_config(base, rtc, __import__("torch"), args.dtype) if args.dtype != "f32" else base
+    stored, true = OracleLoop(cfg), OracleLoop(base)
+    out = {"frames": nframes, "slopes_vs_stored": 0.0, "cmds_vs_stored": 0.0, "cmds_vs_f32_matrix": 0.0}
+    with rtc.Loop(cfg, device=local, telemetry=True) as loop:
+        for k in range(nframes):
+            f = frames[k % len(frames)]
+            loop.process_frame(k + 1, dev_frames[k % len(dev_frames)])
+            fid, a = loop.get_commands(timeout_us=10_000_000)
+            s, _ = loop.get_telemetry(fid, timeout_us=10_000_000)
+            s_ref, a_ref = stored.step(f)
+            _, a_true = true.step(f)
+            rel = lambda x, r: float(np.max(np.abs(x - r)) / max(np.max(np.abs(r)), 1e-30))
+            out["slopes_vs_stored"] = max(out["slopes_vs_stored"], rel(s, s_ref))
+            out["cmds_vs_stored"] = max(out["cmds_vs_stored"], rel(a, a_ref))
+            out["cmds_vs_f32_matrix"] = max(out["cmds_vs_f32_matrix"], rel(a, a_true))
+    out["norm"] = "max over frames of max|x - x_oracle| / max|x_oracle|"
+    return out
+
+
 def quick_arm(args, cfg, frames, rtc, torch, local):
     """Profiling aid: only the unpaced, HBM-resident float32 loop on the chosen workload."""
     dev_frames = []
@@ -552,11 +579,14 @@ def quick_arm(args, cfg, frames, rtc, torch, local):
         srows, _ = run_unpaced_timed(loop, dev_frames, args.steps, args.warmup, sampler, 1)
         info = loop.info()
     lat = stats([r["latency_us"] for r in rows])
+    errors = None
+    if args.errors:
+        errors = format_errors(args, frames, rtc, dev_frames, local)
     mvm = statistics.median([r["mvm_us"] for r in srows])
     sl = statistics.median([r["slopes_us"] for r in srows])
     po = statistics.median([r["polc_us"] for r in srows])
     print(json.dumps({"workload": args.workload, "quick": True, "dtype": args.dtype, "latency_us": lat,
-                      "slopes_us": sl, "polc_us": po, "mvm_us": mvm,
+                      "slopes_us": sl, "polc_us": po, "mvm_us": mvm, "errors": errors,
                       "mvm_gbs": mvm_bytes(info, cfg) / (mvm * 1e-6) / 1e9}), flush=True)
 
 
@@ -663,6 +693,7 @@ def main():
     ap.add_argument("--workload", default="mcao", help="configuration (profiling aid; the bench line is mcao)")
     ap.add_argument("--quick", action="store_true", help="profiling aid: only the unpaced loop")
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "e4m3"], help="matrix storage for --quick")
+    ap.add_argument("--errors", action="store_true", help="--quick: also errors against the FP64 oracle")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -505,12 +505,18 @@ cudaError_t launch_maybe_pdl(K kernel, dim3 grid, const GemvArgs& a, bool pdl, c
     return cudaLaunchKernelEx(&cfg, kernel, a);
 }
 
+#ifndef RTC_GEMV_MIN_WAVES
+#define RTC_GEMV_MIN_WAVES 1
+#endif
+
 template <int DT, int U, int RI>
 cudaError_t launch_gemv_t(const GemvArgs& base, int nb, long long avg_row_bytes, bool pdl, cudaStream_t st) {
-    // rows per warp: as many as keep at least 8 CTAs per SM in flight
+    // rows per warp: as many as keep at least RTC_GEMV_MIN_WAVES waves of 8 CTAs per SM
     const int na = base.na;
     int rpw = 4;
-    while (rpw > RI && (long long)((na + kGemvWarps * rpw - 1) / (kGemvWarps * rpw)) * nb < 8LL * 152) rpw /= 2;
+    while (rpw > RI &&
+           (long long)((na + kGemvWarps * rpw - 1) / (kGemvWarps * rpw)) * nb < RTC_GEMV_MIN_WAVES * 8LL * 152)
+        rpw /= 2;
     GemvArgs a = base;
     a.tiles = (na + kGemvWarps * rpw - 1) / (kGemvWarps * rpw);
     const dim3 grid((unsigned)(a.tiles * nb));

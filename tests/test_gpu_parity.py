@@ -264,6 +264,13 @@ def test_full_size_scao(rtc, torch_cuda, name, nframes):
         run_pair(loop, cfg, frames, nchunks=8)
 
 
+def test_full_size_ltao_chunked(rtc, torch_cuda):
+    cfg = synth.make_config("ltao")
+    frames = synth.draw_frames(cfg, 2, seed=141)
+    with rtc.Loop(cfg, telemetry=True) as loop:
+        run_pair(loop, cfg, frames, mode="chunked", nchunks=8)
+
+
 @pytest.fixture(scope="module")
 def mcao():
     cfg = synth.make_config("mcao")
