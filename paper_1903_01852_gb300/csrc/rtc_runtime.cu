@@ -632,7 +632,8 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
     TRY(dev_alloc(L, &L->d_q, (size_t)L->na * 4));
     CK(L, cudaMemset(L->d_q, 0, (size_t)L->na * 4));
     if (L->has_polc) {
-        CK(L, launch_gemv(L->p_dtype, L->d_P, L->d_pblock, 0, 1, L->na, L->d_a, L->d_Pscale, L->d_q, 0, nullptr, 0, false, L->st));
+        CK(L, launch_gemv(L->p_dtype, L->d_P, L->d_pblock, 0, 1, L->na, L->d_a, L->d_Pscale, L->d_q, 0, nullptr,
+                          (long long)(L->p_bytes / std::max(L->na, 1)), false, L->st));
     }
 
     // ---- page-locked ring, events -------------------------------------------
@@ -1422,7 +1423,8 @@ int rtc_set_state(rtc_loop* L, const float* a, size_t na) {
     CK(L, cudaStreamSynchronize(L->st));
     CK(L, cudaMemcpy(L->d_a, a, na * 4, cudaMemcpyHostToDevice));
     if (L->has_polc)
-        CK(L, launch_gemv(L->p_dtype, L->d_P, L->d_pblock, 0, 1, L->na, L->d_a, L->d_Pscale, L->d_q, 0, nullptr, 0, false, L->st));
+        CK(L, launch_gemv(L->p_dtype, L->d_P, L->d_pblock, 0, 1, L->na, L->d_a, L->d_Pscale, L->d_q, 0, nullptr,
+                          (long long)(L->p_bytes / std::max(L->na, 1)), false, L->st));
     CK(L, cudaStreamSynchronize(L->st));
     return RTC_OK;
 }
