@@ -386,6 +386,17 @@ def cpu_oracle(cfg, frames, nframes=3):
 
 # ---------------------------------------------------------------------------- arms
 
+def max_over_ranks(vals, world, device):
+    """Element-wise maximum of a list of floats over all ranks (identity for one rank)."""
+    if world <= 1:
+        return list(vals)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(vals, device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -525,13 +536,8 @@ def ours_arm(args, world, rank, local):
     for l in loops.values():
         l.close()
 
-    # max over ranks
-    vals = [lat["f32"]["p50"], ms_total / args.steps, float(np.median(e2e_lat))]
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor(vals, device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        vals = t.tolist()
+    # max over ranks (replicas: the slowest replica's latencies)
+    vals = max_over_ranks([lat["f32"]["p50"], ms_total / args.steps, float(np.median(e2e_lat))], world, "cuda")
     if rank != 0:
         return
     traffic = profiled_traffic()
