@@ -19,10 +19,12 @@ definition in float64, in the order the pipeline applies it:
                 slopes; 0 when no pixel is lit
 * pyramid       per valid pupil pixel with quadrant values A (top-left),
                 B (top-right), C (bottom-left), D (bottom-right):
-                N = A+B+C+D, sx = (A+C-B-D)/N, sy = (A+B-C-D)/N, minus reference
+                N = A+B+C+D, sx = (A+C-B-D)/N, sy = (A+B-C-D)/N, minus reference;
+                or, normalised globally, divided by the mean of N over valid pixels
 * MVM           y = M~ s, M~ the matrix actually stored (row scale * code)
 * control law   a_k = (1-leak) a_{k-1} + g (y_k + q_{k-1}), optional clip,
-                q_k = P~ a_k computed after the command (implicit POLC, Section 3.4)
+                q_k = P~ a_k computed after the command (implicit POLC, Section 3.4);
+                or explicit POLC: s_ol = s + D~ a_{k-1}, a_k = (1-leak-g) a_{k-1} + g M~ s_ol
 
 Slope order: interleaved (x, y) per valid unit, units in row-major order of the
 subaperture grid (or pupil pixels), WFS after WFS in configuration order.
@@ -101,18 +103,33 @@ def sh_slopes(raw, w):
 def pyramid_slopes(raw, w):
     """Normalised quad-difference slopes of one pyramid WFS (Fig. wfs_slopes:
     relative x and y differences of corresponding pixels of the four pupil
-    images), interleaved x,y over valid pupil pixels in row-major order."""
+    images), interleaved x,y over valid pupil pixels in row-major order.
+
+    w["norm"] "local" (default): each pixel's differences are divided by its own
+    flux N = A+B+C+D.  "global": they are divided by the mean of N over the
+    valid pupil pixels; every slope is 0 when that mean is not positive."""
     t, lit = calibrate(raw, w["dark"], w["flat"], w["threshold"], w["thresh_mode"])
     p = w["pupil"]
     quad = [t[w["qy"][k]:w["qy"][k] + p, w["qx"][k]:w["qx"][k] + p] for k in range(4)]
     qlit = [lit[w["qy"][k]:w["qy"][k] + p, w["qx"][k]:w["qx"][k] + p] for k in range(4)]
     a, b, c, d = quad
     total = a + b + c + d
-    any_lit = (qlit[0] | qlit[1] | qlit[2] | qlit[3]) & (total > 0)
-    safe = np.where(any_lit, total, 1.0)
-    sx = np.where(any_lit, (a + c - b - d) / safe, 0.0)
-    sy = np.where(any_lit, (a + b - c - d) / safe, 0.0)
     v = w["valid"].astype(bool)
+    norm = w.get("norm", "local")
+    if norm == "local":
+        any_lit = (qlit[0] | qlit[1] | qlit[2] | qlit[3]) & (total > 0)
+        safe = np.where(any_lit, total, 1.0)
+        sx = np.where(any_lit, (a + c - b - d) / safe, 0.0)
+        sy = np.where(any_lit, (a + b - c - d) / safe, 0.0)
+    elif norm == "global":
+        mean_flux = total[v].mean() if v.any() else 0.0
+        if mean_flux > 0:
+            sx = (a + c - b - d) / mean_flux
+            sy = (a + b - c - d) / mean_flux
+        else:
+            sx = sy = np.zeros_like(total)
+    else:
+        raise ValueError(norm)
     return np.stack([sx[v], sy[v]], axis=1).reshape(-1)
 
 
@@ -247,13 +264,22 @@ def explicit_polc_step(m64, d64, s, a_prev, gain, leak):
 
 
 class OracleLoop:
-    """One AO loop in float64: holds M~, P~ and the integrator state."""
+    """One AO loop in float64: holds M~, P~ (or D~) and the integrator state.
+
+    cfg["polc"] "implicit" (default): the control law above, with q = P~ a.
+    "explicit": the pseudo-open-loop slopes s_ol = s + D~ a_{k-1} are formed
+    first and a_k = (1 - leak - gain) a_{k-1} + gain M~ s_ol (Section 3.4's
+    explicit form; D is the ns x na interaction matrix); step() then returns
+    s_ol as the slopes, since they are what the reconstructor is applied to."""
 
     def __init__(self, cfg):
         self.cfg = cfg
+        self.explicit = cfg.get("polc", "implicit") == "explicit"
         self.m = stored_matrix(cfg["M"], cfg.get("M_dtype", "f32"), cfg.get("M_scale"))
         self.p = (stored_matrix(cfg["P"], cfg.get("P_dtype", "f32"), cfg.get("P_scale"))
-                  if cfg.get("P") is not None else None)
+                  if cfg.get("P") is not None and not self.explicit else None)
+        self.d = (stored_matrix(cfg["D"], cfg.get("D_dtype", "f32"), cfg.get("D_scale"))
+                  if self.explicit else None)
         na = self.m.shape[0]
         a0 = cfg.get("a0")
         self.a = np.zeros(na) if a0 is None else np.asarray(a0, dtype=f64).copy()
@@ -262,8 +288,15 @@ class OracleLoop:
     def step(self, frames):
         """One frame: returns (slopes, commands) and advances the state."""
         s = frame_slopes(self.cfg, frames)
+        gain, leak, clip = self.cfg["gain"], self.cfg["leak"], self.cfg.get("clip")
+        if self.explicit:
+            s = s + self.d @ self.a           # pseudo-open-loop slopes
+            self.a = (1.0 - leak - gain) * self.a + gain * mvm(self.m, s)
+            if clip is not None:
+                self.a = np.clip(self.a, clip[0], clip[1])
+            return s, self.a.copy()
         y = mvm(self.m, s)
-        self.a = control_step(self.a, y, self.q, self.cfg["gain"], self.cfg["leak"], self.cfg.get("clip"))
+        self.a = control_step(self.a, y, self.q, gain, leak, clip)
         if self.p is not None:
             self.q = self.p @ self.a          # for the next frame, after the command is out
         return s, self.a.copy()

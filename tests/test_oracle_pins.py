@@ -251,6 +251,77 @@ def test_pyramid_equal_quadrants_zero():
     assert not orc.pyramid_slopes(raw, w).any()
 
 
+def test_pyramid_global_norm_hand_values():
+    # one lit quadrant per pupil pixel: fluxes 8, 4, 2, 2 (mean 4)
+    p = 2
+    w = pyr_desc(p)
+    w["norm"] = "global"
+    raw = np.zeros((w["height"], w["width"]), np.uint16)
+    for (i, j), k, v in [((0, 0), 0, 8), ((0, 1), 1, 4), ((1, 0), 2, 2), ((1, 1), 3, 2)]:
+        raw[w["qy"][k] + i, w["qx"][k] + j] = v
+    assert orc.pyramid_slopes(raw, w).tolist() == [2.0, 2.0, -1.0, 1.0, 0.5, -0.5, -0.5, -0.5]
+    w["norm"] = "local"
+    assert orc.pyramid_slopes(raw, w).tolist() == [1.0, 1.0, -1.0, 1.0, 1.0, -1.0, -1.0, -1.0]
+
+
+def test_pyramid_global_norm_closed_form_with_varying_flux():
+    # A = N_p/4 (1+sx+sy) etc.: local normalisation returns (sx, sy); global
+    # normalisation returns (sx, sy) * N_p / mean(N) over the valid pixels.
+    rng = np.random.default_rng(15)
+    p = 6
+    w = pyr_desc(p)
+    valid = (rng.random((p, p)) > 0.25).astype(np.uint8)
+    w["valid"] = valid
+    w["norm"] = "global"
+    sx = rng.uniform(-0.45, 0.45, size=(p, p))
+    sy = rng.uniform(-0.45, 0.45, size=(p, p))
+    n = rng.uniform(500.0, 3000.0, size=(p, p))
+    quads = [n / 4 * (1 + sx + sy), n / 4 * (1 - sx + sy), n / 4 * (1 + sx - sy), n / 4 * (1 - sx - sy)]
+    w["flat"] = np.zeros_like(w["flat"])
+    for k in range(4):
+        w["flat"][w["qy"][k]:w["qy"][k] + p, w["qx"][k]:w["qx"][k] + p] = quads[k]
+    got = orc.pyramid_slopes(np.ones((w["height"], w["width"]), np.uint16), w).reshape(-1, 2)
+    v = valid.astype(bool)
+    factor = n[v] / n[v].mean()
+    assert np.allclose(got[:, 0], sx[v] * factor, rtol=0, atol=1e-6)
+    assert np.allclose(got[:, 1], sy[v] * factor, rtol=0, atol=1e-6)
+
+
+def test_pyramid_global_norm_uniform_flux_equals_local_and_ignores_invalid_pixels():
+    rng = np.random.default_rng(16)
+    p = 5
+    w = pyr_desc(p)
+    valid = np.ones((p, p), np.uint8)
+    valid[2, 3] = 0
+    w["valid"] = valid
+    sx = rng.integers(-25, 26, size=(p, p)) / 64.0          # dyadic: every intensity is exact in float32,
+    sy = rng.integers(-25, 26, size=(p, p)) / 64.0          # so every pixel's flux is exactly 1024
+    quads = [256 * (1 + sx + sy), 256 * (1 - sx + sy), 256 * (1 + sx - sy), 256 * (1 - sx - sy)]
+    w["flat"] = np.zeros_like(w["flat"])
+    for k in range(4):
+        w["flat"][w["qy"][k]:w["qy"][k] + p, w["qx"][k]:w["qx"][k] + p] = quads[k]
+    raw = np.ones((w["height"], w["width"]), np.uint16)
+    loc = orc.pyramid_slopes(raw, dict(w, norm="local"))
+    glo = orc.pyramid_slopes(raw, dict(w, norm="global"))
+    assert np.allclose(glo, loc, rtol=0, atol=1e-15)
+    # flux in the invalid pupil pixel does not enter the mean
+    for k in range(4):
+        w["flat"][w["qy"][k] + 2, w["qx"][k] + 3] = 5000.0
+    assert np.allclose(orc.pyramid_slopes(raw, dict(w, norm="global")), loc, rtol=0, atol=1e-15)
+    # a common factor on every intensity cancels
+    w2 = dict(w, norm="global", flat=w["flat"] * 2)
+    assert np.allclose(orc.pyramid_slopes(raw, w2), loc, rtol=0, atol=1e-15)
+
+
+def test_pyramid_global_norm_zero_flux_gives_zero_slopes():
+    w = pyr_desc(3)
+    w["norm"] = "global"
+    w["threshold"] = 10.0
+    raw = np.full((w["height"], w["width"]), 10, np.uint16)
+    out = orc.pyramid_slopes(raw, w)
+    assert out.shape == (18,) and not out.any() and np.isfinite(out).all()
+
+
 # ---------------------------------------------------------------- quantisation
 
 torch = pytest.importorskip("torch")
@@ -371,6 +442,48 @@ def test_implicit_polc_equals_explicit_polc():
         q = P @ a_imp
         a_exp = orc.explicit_polc_step(M, D, s, a_exp, g, leak)
         assert np.allclose(a_imp, a_exp, rtol=0, atol=1e-12)
+
+
+def _polc_cfgs(rng, n=4, nsub=2, na=5):
+    w = sh_desc(n, nsub=nsub)
+    ns = 2 * nsub * nsub
+    # small dyadic entries: P = M D - I is exact in float32, so both loops use the same matrices
+    M = (rng.integers(-8, 9, size=(na, ns)) / 16.0).astype(np.float32)
+    D = (rng.integers(-8, 9, size=(ns, na)) / 16.0).astype(np.float32)
+    P = (M.astype(np.float64) @ D.astype(np.float64) - np.eye(na)).astype(np.float32)
+    assert np.array_equal(P.astype(np.float64), M.astype(np.float64) @ D.astype(np.float64) - np.eye(na))
+    base = dict(wfs=[w], M=M, gain=0.5, leak=0.01, ref_slopes=None)
+    return dict(base, P=P), dict(base, polc="explicit", D=D), M, D
+
+
+def test_oracle_loop_explicit_polc_equals_implicit_with_p_eq_md_minus_i():
+    rng = np.random.default_rng(17)
+    imp_cfg, exp_cfg, M, D = _polc_cfgs(rng)
+    imp, exp = orc.OracleLoop(imp_cfg), orc.OracleLoop(exp_cfg)
+    for _ in range(10):
+        raw = rng.integers(0, 50, size=(8, 8)).astype(np.uint16)
+        a_prev = exp.a.copy()
+        s_i, a_i = imp.step([raw])
+        s_e, a_e = exp.step([raw])
+        assert np.allclose(s_e, s_i + D.astype(np.float64) @ a_prev, rtol=0, atol=1e-12)   # POL slopes
+        assert np.allclose(a_e, a_i, rtol=0, atol=1e-12)
+
+
+def test_oracle_loop_explicit_polc_with_d_zero_closed_form():
+    # D = 0: a_k = (1 - leak - g) a_{k-1} + g y, so a_k = g y (1 - (1-leak-g)^k) / (leak + g)
+    n = 4
+    w = sh_desc(n)
+    raw = np.zeros((n, n), np.uint16)
+    raw[0, 3] = 10                        # slopes (1.5, -1.5)
+    g, leak = 0.25, 0.125
+    cfg = dict(wfs=[w], M=np.array([[2.0, 1.0], [0.0, -4.0]], np.float32), gain=g, leak=leak,
+               ref_slopes=None, polc="explicit", D=np.zeros((2, 2), np.float32))
+    loop = orc.OracleLoop(cfg)
+    y = np.array([2.0 * 1.5 - 1.5, 6.0])
+    for k in range(1, 8):
+        s, a = loop.step([raw])
+        assert s.tolist() == [1.5, -1.5]
+        assert np.allclose(a, g * y * (1 - (1 - leak - g) ** k) / (leak + g), rtol=1e-14, atol=0)
 
 
 def test_oracle_loop_one_frame_identity_matrix():
