@@ -63,6 +63,12 @@ extern "C" {
 #define RTC_THRESH_SUBTRACT 0  /* t = max(c - T, 0) */
 #define RTC_THRESH_CLIP     1  /* t = c if c > T else 0 */
 
+#define RTC_NORM_LOCAL  0   /* pyramid: divide by each pixel's own flux A+B+C+D */
+#define RTC_NORM_GLOBAL 1   /* pyramid: divide by the mean flux over the valid pupil pixels */
+
+#define RTC_POLC_IMPLICIT 0 /* q = P a added to the reconstruction (Section 3.4, implicit form) */
+#define RTC_POLC_EXPLICIT 1 /* s + D a formed before the reconstruction (explicit form) */
+
 #define RTC_FLAG_TIMING     1u /* record frame-level CUDA events (rtc_get_timing) */
 #define RTC_FLAG_TELEMETRY  2u /* copy slopes of every frame to the page-locked ring */
 #define RTC_FLAG_STAGE_TIMING 4u /* also time the slope and MVM kernels separately; this
@@ -89,7 +95,13 @@ extern "C" {
  * into, by whole slope rows (subaperture rows or pupil rows), as evenly as
  * possible; a block's MVM starts as soon as its pixel rows have arrived
  * (Section 2.2: centroiding starts when a row of subapertures is complete).
- * 1 <= nblocks <= number of slope rows. */
+ * 1 <= nblocks <= number of slope rows.
+ * norm (pyramid only; 0 for SH): RTC_NORM_LOCAL divides each pupil pixel's
+ * quad differences by its own flux N = A+B+C+D (Fig. wfs_slopes, "relative
+ * differences"); RTC_NORM_GLOBAL divides them by the mean of N over the valid
+ * pupil pixels (every slope 0 when that mean is not positive).  A globally
+ * normalised WFS computes its slopes, and starts its column blocks' MVM, only
+ * once its whole frame has arrived, since every slope needs every pixel. */
 typedef struct rtc_wfs {
     int32_t kind;
     int32_t width, height;
@@ -97,6 +109,7 @@ typedef struct rtc_wfs {
     int32_t pupil, qx[4], qy[4];         /* pyramid only */
     const uint8_t* valid;
     int32_t nblocks;
+    int32_t norm;                        /* RTC_NORM_* (pyramid only) */
 } rtc_wfs;
 
 /* The loop's sensors and run-time options. */
@@ -137,13 +150,22 @@ typedef struct rtc_cmat {
     const float* row_scale;
 } rtc_cmat;
 
-/* Control law with implicit POLC (Section 3.4):
+/* Control law.  mode RTC_POLC_IMPLICIT (0), implicit POLC (Section 3.4):
  *   a_k = (1 - leak) a_{k-1} + gain (M s_k + q_{k-1}),  q_k = P a_k,
  * then the optional clip to [amin, amax].  q_k is computed after frame k's
  * commands are ready, for frame k+1, off the latency path.
  * P: host row-major na x na of element type dtype with optional row_scale,
  * or NULL for a plain leaky integrator (q = 0).  a0: host float32[na]
- * initial commands, or NULL for zeros. */
+ * initial commands, or NULL for zeros.
+ * mode RTC_POLC_EXPLICIT (1), the explicit form of Section 3.4: the
+ * pseudo-open-loop slopes s_ol = s_k + u_{k-1} are formed first, with
+ * u_k = D a_k computed after frame k's commands (off the latency path), and
+ *   a_k = (1 - leak - gain) a_{k-1} + gain M s_ol,  then the optional clip.
+ * D: host row-major ns x na interaction matrix of element type d_dtype with
+ * optional d_row_scale (float32[ns]); required in this mode, and P must be
+ * NULL.  The telemetry slopes of such a loop are s_ol.  With P = M D - I the
+ * two modes give the same commands; the explicit one streams ns x na matrix
+ * elements per frame for the POLC term instead of na x na. */
 typedef struct rtc_polc {
     const void* P;
     int32_t dtype;
@@ -152,6 +174,10 @@ typedef struct rtc_polc {
     const float* a0;
     int32_t clip;
     float amin, amax;
+    int32_t mode;                /* RTC_POLC_* */
+    const void* D;               /* explicit mode: ns x na, or NULL */
+    int32_t d_dtype;
+    const float* d_row_scale;
 } rtc_polc;
 
 typedef struct rtc_loop rtc_loop;   /* opaque */
@@ -258,7 +284,8 @@ int rtc_get_timing(rtc_loop* loop, uint64_t frame_id, rtc_timing* out, int64_t t
  * shapes and element types are those given at creation.  M: host row-major
  * na x ns in the loop's matrix type, with M_scale (float32[na]) when the loop
  * was created with row scales (NULL keeps the current scales).  P / P_scale:
- * the same for the POLC matrix (loop created with POLC).  dark / flat: arrays
+ * the same for the POLC matrix (loop created with implicit POLC; the D of an
+ * explicit-POLC loop is fixed at creation, and a P for it is RTC_EINVAL).  dark / flat: arrays
  * of nwfs host pointers (entries may be NULL).  threshold: nwfs values or NULL.
  * ref_slopes: ns values.  set_control non-zero replaces gain, leak and the clip. */
 typedef struct rtc_update_desc {
@@ -292,7 +319,8 @@ int rtc_update(rtc_loop* loop, const rtc_update_desc* desc);
 
 /* Wait for queued work, then copy the integrator state a (na floats) out. */
 int rtc_get_state(rtc_loop* loop, float* a, size_t na);
-/* Wait for queued work, then set a and recompute q = P a (checkpoint resume). */
+/* Wait for queued work, then set a and recompute q = P a, or u = D a in
+ * explicit-POLC mode (checkpoint resume). */
 int rtc_set_state(rtc_loop* loop, const float* a, size_t na);
 /* Wait for all queued work of the loop. */
 int rtc_sync(rtc_loop* loop);

@@ -22,6 +22,8 @@ RTC_EORDER, RTC_EDROPPED, RTC_ECUDA, RTC_ENOENT = -4, -5, -6, -7
 RTC_WFS_SH, RTC_WFS_PYRAMID = 0, 1
 RTC_F32, RTC_BF16, RTC_E4M3 = 0, 1, 2
 RTC_THRESH_SUBTRACT, RTC_THRESH_CLIP = 0, 1
+RTC_NORM_LOCAL, RTC_NORM_GLOBAL = 0, 1
+RTC_POLC_IMPLICIT, RTC_POLC_EXPLICIT = 0, 1
 RTC_FLAG_TIMING, RTC_FLAG_TELEMETRY, RTC_FLAG_STAGE_TIMING, RTC_FLAG_UPDATABLE, RTC_FLAG_GRAPHS = 1, 2, 4, 8, 16
 RTC_MAX_WFS = 16
 DTYPES = {"f32": RTC_F32, "bf16": RTC_BF16, "e4m3": RTC_E4M3}
@@ -36,7 +38,7 @@ class rtc_wfs(C.Structure):
     _fields_ = [("kind", C.c_int32), ("width", C.c_int32), ("height", C.c_int32),
                 ("nsubx", C.c_int32), ("nsuby", C.c_int32), ("npx", C.c_int32), ("ox", C.c_int32),
                 ("oy", C.c_int32), ("pupil", C.c_int32), ("qx", C.c_int32 * 4), ("qy", C.c_int32 * 4),
-                ("valid", C.POINTER(C.c_uint8)), ("nblocks", C.c_int32)]
+                ("valid", C.POINTER(C.c_uint8)), ("nblocks", C.c_int32), ("norm", C.c_int32)]
 
 
 class rtc_geometry(C.Structure):
@@ -57,7 +59,8 @@ class rtc_cmat(C.Structure):
 class rtc_polc(C.Structure):
     _fields_ = [("P", C.c_void_p), ("dtype", C.c_int32), ("row_scale", f32p), ("gain", C.c_float),
                 ("leak", C.c_float), ("a0", f32p), ("clip", C.c_int32), ("amin", C.c_float),
-                ("amax", C.c_float)]
+                ("amax", C.c_float), ("mode", C.c_int32), ("D", C.c_void_p), ("d_dtype", C.c_int32),
+                ("d_row_scale", f32p)]
 
 
 class rtc_chunk(C.Structure):
@@ -210,6 +213,7 @@ def describe(cfg, device=0, flags=0, ring=4):
             s.pupil = w["pupil"]
             for q in range(4):
                 s.qx[q], s.qy[q] = w["qx"][q], w["qy"][q]
+            s.norm = RTC_NORM_GLOBAL if w.get("norm", "local") == "global" else RTC_NORM_LOCAL
         v = np.ascontiguousarray(w["valid"], dtype=np.uint8)
         keep.append(v)
         s.valid = v.ctypes.data_as(C.POINTER(C.c_uint8))
@@ -231,9 +235,17 @@ def describe(cfg, device=0, flags=0, ring=4):
     ps = _f32(cfg.get("P_scale"))
     a0 = _f32(cfg.get("a0"))
     clip = cfg.get("clip")
+    explicit = cfg.get("polc", "implicit") == "explicit"
+    if explicit:
+        Pa = ps = None
+    ddt = DTYPES[cfg.get("D_dtype", "f32")]
+    Da = np.ascontiguousarray(cfg["D"], dtype=CODE_NP[ddt]) if explicit else None
+    dsc = _f32(cfg.get("D_scale")) if explicit else None
     st.pol = rtc_polc(None if Pa is None else Pa.ctypes.data, pdt, _fptr(ps), float(cfg["gain"]), float(cfg["leak"]),
-                      _fptr(a0), 1 if clip else 0, float(clip[0]) if clip else 0.0, float(clip[1]) if clip else 0.0)
-    st.keep = keep + [warr, darks, flats, thr, mode, ref, M, ms, Pa, ps, a0]
+                      _fptr(a0), 1 if clip else 0, float(clip[0]) if clip else 0.0, float(clip[1]) if clip else 0.0,
+                      RTC_POLC_EXPLICIT if explicit else RTC_POLC_IMPLICIT, None if Da is None else Da.ctypes.data,
+                      ddt, _fptr(dsc))
+    st.keep = keep + [warr, darks, flats, thr, mode, ref, M, ms, Pa, ps, a0, Da, dsc]
     return st
 
 

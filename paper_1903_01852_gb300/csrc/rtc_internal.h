@@ -26,6 +26,13 @@ struct WfsDev {
     const float* flat;
     int calib_pitch;          // floats per calibration-map row (multiple of 4)
     int sh_groups;            // SH: row groups per CTA in the column-sum phase
+    // pyramid with global normalisation (norm == RTC_NORM_GLOBAL): its slope rows
+    // are always launched together; the last of them to finish normalises all
+    int norm;
+    int grow0, gnrows;        // its slope rows in the row table
+    int gblk0, gnblk;         // its column blocks
+    int gpix;                 // valid pupil pixels
+    int gflux;                // float offset of the per-row flux sums in the part scratch
 };
 
 // One slope row: a subaperture row (SH) or a pupil row (pyramid).
@@ -90,10 +97,12 @@ int elems_per_16B(int dtype);
 // Opt the slope kernel in to more than 48 KB of dynamic shared memory when needed.
 cudaError_t configure_slopes(int smem_bytes);
 
-// Slope kernel over the part table entries [part0, part0 + nparts).
+// Slope kernel over the part table entries [part0, part0 + nparts).  Each slope
+// is (measured - ref) + pol, with ref and pol (compact slope order) optional;
+// blocks (the column-block table) locates a globally normalised WFS's slopes.
 cudaError_t launch_slopes(const SlopePart* parts, int part0, int nparts, const SlopeRow* rows,
-                          const WfsDev* wfs, const FramePtrs& fp, const uint16_t* xlist,
-                          const float* ref, float* s_pad, float* pscr, unsigned* counters,
+                          const WfsDev* wfs, const BlockDev* blocks, const FramePtrs& fp, const uint16_t* xlist,
+                          const float* ref, const float* pol, float* s_pad, float* pscr, unsigned* counters,
                           int smem_bytes, cudaStream_t st);
 
 // GEMV over blocks [b0, b0 + nb): out[b * out_stride + r] = sum_j M_b[r][j] x[x_off_b + j],

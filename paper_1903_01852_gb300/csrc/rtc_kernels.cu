@@ -49,6 +49,15 @@ __device__ __forceinline__ float calibrate(unsigned raw, float dark, float flat,
     return mode == RTC_THRESH_SUBTRACT ? __fsub_rn(c, T) : c;
 }
 
+// A slope pair as stored: (measured - reference) + pseudo-open-loop term.
+__device__ __forceinline__ void store_pair(float* __restrict__ s_pad, int pad, const float* __restrict__ ref,
+                                           const float* __restrict__ pol, int comp, float sx, float sy) {
+    if (ref) { sx -= ref[comp]; sy -= ref[comp + 1]; }
+    if (pol) { sx += pol[comp]; sy += pol[comp + 1]; }
+    s_pad[pad] = sx;
+    s_pad[pad + 1] = sy;
+}
+
 // SH slope-row part: pixel rows [pr0, pr1) of one subaperture row.  The CTA
 // first reduces each pixel column of the strip over its rows (column flux F_c
 // and first moment in y), in G row groups so that narrow strips still use the
@@ -59,8 +68,8 @@ __device__ __forceinline__ float calibrate(unsigned raw, float dark, float flat,
 // part order and writes the slopes.  Every sum has a fixed order.
 __device__ void sh_part(const SlopePart& P, const SlopeRow& row, const WfsDev& W, const uint16_t* __restrict__ px,
                         long long pitch, int prow0, const uint16_t* __restrict__ xlist, const float* __restrict__ ref,
-                        float* __restrict__ s_pad, float* __restrict__ pscr, unsigned* __restrict__ counters,
-                        float* sm) {
+                        const float* __restrict__ pol, float* __restrict__ s_pad, float* __restrict__ pscr,
+                        unsigned* __restrict__ counters, float* sm) {
     __shared__ int s_last;
     const int n = W.npx;
     const int ws = W.nsubx * n;                 // strip width in pixels
@@ -132,9 +141,7 @@ __device__ void sh_part(const SlopePart& P, const SlopeRow& row, const WfsDev& W
         if (single) {
             float sx = 0.f, sy = 0.f;
             if (Fs > 0.f) { sx = Xs / Fs; sy = Ys / Fs; }
-            if (ref) { sx -= ref[row.s_compact + 2 * u]; sy -= ref[row.s_compact + 2 * u + 1]; }
-            s_pad[row.s_pad + 2 * u] = sx;
-            s_pad[row.s_pad + 2 * u + 1] = sy;
+            store_pair(s_pad, row.s_pad + 2 * u, ref, pol, row.s_compact + 2 * u, sx, sy);
         } else {
             float* o = pscr + row.pscr + 3 * ((size_t)P.part * row.nunits + u);
             o[0] = Fs; o[1] = Xs; o[2] = Ys;
@@ -189,9 +196,7 @@ __device__ void sh_part(const SlopePart& P, const SlopeRow& row, const WfsDev& W
         }
         float sx = 0.f, sy = 0.f;
         if (Fs > 0.f) { sx = Xs / Fs; sy = Ys / Fs; }
-        if (ref) { sx -= ref[row.s_compact + 2 * u]; sy -= ref[row.s_compact + 2 * u + 1]; }
-        s_pad[row.s_pad + 2 * u] = sx;
-        s_pad[row.s_pad + 2 * u + 1] = sy;
+        store_pair(s_pad, row.s_pad + 2 * u, ref, pol, row.s_compact + 2 * u, sx, sy);
     }
     if (threadIdx.x == 0) counters[P.row] = 0u;
 }
@@ -199,10 +204,17 @@ __device__ void sh_part(const SlopePart& P, const SlopeRow& row, const WfsDev& W
 // Pyramid slope row: one thread per valid pupil pixel reads the matching pixel
 // of the four pupil images A (top-left), B (top-right), C (bottom-left),
 // D (bottom-right); sx = (A+C-B-D)/N, sy = (A+B-C-D)/N with N = A+B+C+D.
-__device__ void pyr_row(const SlopeRow& row, const WfsDev& W, const uint16_t* __restrict__ px,
-                        long long pitch, int prow0, const uint16_t* __restrict__ xlist,
-                        const float* __restrict__ ref, float* __restrict__ s_pad) {
+// With global normalisation the row stores the differences themselves and its
+// flux sum; the last row of the WFS to finish (they are launched together)
+// divides every difference by the mean flux over the valid pupil pixels.
+__device__ void pyr_row(const SlopeRow& row, const WfsDev& W, const BlockDev* __restrict__ blocks,
+                        const uint16_t* __restrict__ px, long long pitch, int prow0,
+                        const uint16_t* __restrict__ xlist, const float* __restrict__ ref,
+                        const float* __restrict__ pol, float* __restrict__ s_pad, float* __restrict__ pscr,
+                        unsigned* __restrict__ counters) {
     const int i = row.row;
+    const bool global = W.norm == RTC_NORM_GLOBAL;
+    float flux = 0.f;
     for (int u = threadIdx.x; u < row.nunits; u += blockDim.x) {
         const int j = xlist[row.unit0 + u];
         float v[4];
@@ -214,15 +226,71 @@ __device__ void pyr_row(const SlopeRow& row, const WfsDev& W, const uint16_t* __
                              W.thresh_mode);
         }
         const float N = (v[0] + v[1]) + (v[2] + v[3]);
-        float sx = 0.f, sy = 0.f;
-        if (N > 0.f) {
-            sx = ((v[0] + v[2]) - (v[1] + v[3])) / N;
-            sy = ((v[0] + v[1]) - (v[2] + v[3])) / N;
+        const float dx = (v[0] + v[2]) - (v[1] + v[3]);
+        const float dy = (v[0] + v[1]) - (v[2] + v[3]);
+        if (global) {
+            flux += N;
+            s_pad[row.s_pad + 2 * u] = dx;
+            s_pad[row.s_pad + 2 * u + 1] = dy;
+            continue;
         }
-        if (ref) { sx -= ref[row.s_compact + 2 * u]; sy -= ref[row.s_compact + 2 * u + 1]; }
-        s_pad[row.s_pad + 2 * u] = sx;
-        s_pad[row.s_pad + 2 * u + 1] = sy;
+        float sx = 0.f, sy = 0.f;
+        if (N > 0.f) { sx = dx / N; sy = dy / N; }
+        store_pair(s_pad, row.s_pad + 2 * u, ref, pol, row.s_compact + 2 * u, sx, sy);
     }
+    if (!global) return;
+
+    // row flux: per-thread sums in unit order, then a fixed reduction over the CTA
+    __shared__ float s_red[kSlopeThreads / 32];
+    __shared__ int s_last;
+    __shared__ float s_mean;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    flux = warp_sum(flux);
+    if (lane == 0) s_red[warp] = flux;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float f = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) f += s_red[w];
+        pscr[W.gflux + i] = f;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&counters[W.grow0], 1u) == (unsigned)(W.gnrows - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (warp == 0) {
+        float f = 0.f;
+        for (int r = lane; r < W.gnrows; r += 32) f += __ldcg(pscr + W.gflux + r);
+        f = warp_sum(f);
+        if (lane == 0) s_mean = f / float(W.gpix);
+    }
+    __syncthreads();
+    const float mean = s_mean;
+    // every slope pair of the WFS, block by block; eight pairs of loads in flight per thread
+    constexpr int kU = 8;
+    for (int b = W.gblk0; b < W.gblk0 + W.gnblk; ++b) {
+        const BlockDev B = blocks[b];
+        const int npair = B.ncols >> 1;
+        for (int q0 = threadIdx.x; q0 < npair; q0 += kU * blockDim.x) {
+            float2 d[kU];
+#pragma unroll
+            for (int k = 0; k < kU; ++k) {
+                const int q = q0 + k * blockDim.x;
+                d[k] = q < npair ? __ldcg(reinterpret_cast<const float2*>(s_pad + B.x_off) + q) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int k = 0; k < kU; ++k) {
+                const int q = q0 + k * blockDim.x;
+                if (q < npair) {
+                    float sx = 0.f, sy = 0.f;
+                    if (mean > 0.f) { sx = d[k].x / mean; sy = d[k].y / mean; }
+                    store_pair(s_pad, B.x_off + 2 * q, ref, pol, B.c0 + 2 * q, sx, sy);
+                }
+            }
+        }
+    }
+    if (threadIdx.x == 0) counters[W.grow0] = 0u;
 }
 
 struct SlopeArgs {
@@ -230,9 +298,11 @@ struct SlopeArgs {
     int part0;
     const SlopeRow* rows;
     const WfsDev* wfs;
+    const BlockDev* blocks;
     FramePtrs fp;
     const uint16_t* xlist;
     const float* ref;
+    const float* pol;
     float* s_pad;
     float* pscr;
     unsigned* counters;
@@ -245,10 +315,11 @@ __global__ void __launch_bounds__(kSlopeThreads) slopes_kernel(const __grid_cons
     const SlopeRow row = a.rows[P.row];
     const WfsDev W = a.wfs[row.wfs];
     if (W.kind == RTC_WFS_SH)
-        sh_part(P, row, W, a.fp.px[row.wfs], a.fp.pitch[row.wfs], a.fp.row0[row.wfs], a.xlist, a.ref, a.s_pad, a.pscr,
-                a.counters, sm);
+        sh_part(P, row, W, a.fp.px[row.wfs], a.fp.pitch[row.wfs], a.fp.row0[row.wfs], a.xlist, a.ref, a.pol, a.s_pad,
+                a.pscr, a.counters, sm);
     else
-        pyr_row(row, W, a.fp.px[row.wfs], a.fp.pitch[row.wfs], a.fp.row0[row.wfs], a.xlist, a.ref, a.s_pad);
+        pyr_row(row, W, a.blocks, a.fp.px[row.wfs], a.fp.pitch[row.wfs], a.fp.row0[row.wfs], a.xlist, a.ref, a.pol,
+                a.s_pad, a.pscr, a.counters);
 }
 
 cudaError_t configure_slopes(int smem_bytes) {
@@ -257,10 +328,11 @@ cudaError_t configure_slopes(int smem_bytes) {
 }
 
 cudaError_t launch_slopes(const SlopePart* parts, int part0, int nparts, const SlopeRow* rows, const WfsDev* wfs,
-                          const FramePtrs& fp, const uint16_t* xlist, const float* ref, float* s_pad, float* pscr,
-                          unsigned* counters, int smem_bytes, cudaStream_t st) {
+                          const BlockDev* blocks, const FramePtrs& fp, const uint16_t* xlist, const float* ref,
+                          const float* pol, float* s_pad, float* pscr, unsigned* counters, int smem_bytes,
+                          cudaStream_t st) {
     if (nparts <= 0) return cudaSuccess;
-    SlopeArgs a{parts, part0, rows, wfs, fp, xlist, ref, s_pad, pscr, counters};
+    SlopeArgs a{parts, part0, rows, wfs, blocks, fp, xlist, ref, pol, s_pad, pscr, counters};
     slopes_kernel<<<nparts, kSlopeThreads, smem_bytes, st>>>(a);
     return cudaGetLastError();
 }

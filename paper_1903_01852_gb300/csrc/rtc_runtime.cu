@@ -47,6 +47,7 @@ struct rtc_loop {
     float gain = 0.f, leak = 0.f, amin = 0.f, amax = 0.f;
     int clip = 0;
     bool has_polc = false, timing = false, telemetry = false, stage_timing = false;
+    bool explicit_polc = false;     // s + D a formed before the reconstruction (RTC_POLC_EXPLICIT)
 
     // host plans
     std::vector<rtc_wfs> wfs;
@@ -81,6 +82,10 @@ struct rtc_loop {
     float* d_part = nullptr;
     float* d_a = nullptr;
     float* d_q = nullptr;
+    void* d_D = nullptr;                    // explicit POLC: ns x na interaction matrix, one column block
+    float* d_Dscale = nullptr;
+    BlockDev* d_dblock = nullptr;
+    float* d_u = nullptr;                   // explicit POLC: u = D a (ns, compact slope order)
     std::vector<void*> allocs;              // everything cudaMalloc'd, for destroy
 
     // page-locked ring: per slot na commands then ns slopes
@@ -261,12 +266,14 @@ int check_wfs(const rtc_wfs& w, int k) {
             return bad("SH grid outside the frame");
         if (w.nsubx > 65535) return bad("too many subapertures across");
         if (w.nblocks < 1 || w.nblocks > w.nsuby) return bad("nblocks must be in [1, nsuby]");
+        if (w.norm != RTC_NORM_LOCAL) return bad("norm applies to pyramid WFS only");
     } else if (w.kind == RTC_WFS_PYRAMID) {
         if (w.pupil <= 0) return bad("bad pupil size");
         for (int q = 0; q < 4; ++q)
             if (w.qx[q] < 0 || w.qy[q] < 0 || w.qx[q] + w.pupil > w.width || w.qy[q] + w.pupil > w.height)
                 return bad("pupil image outside the frame");
         if (w.nblocks < 1 || w.nblocks > w.pupil) return bad("nblocks must be in [1, pupil]");
+        if (w.norm != RTC_NORM_LOCAL && w.norm != RTC_NORM_GLOBAL) return bad("bad norm");
     } else {
         return bad("unknown kind");
     }
@@ -309,6 +316,18 @@ int upload_matrix(rtc_loop* L, int dtype, const void* host, int rows, int cols, 
     return rc;
 }
 
+// The POLC product for the next frame from the current commands a: q = P a
+// (implicit) or u = D a (explicit), on the loop stream.
+int polc_product(rtc_loop* L, bool pdl) {
+    if (L->has_polc)
+        CK(L, launch_gemv(L->p_dtype, L->d_P, L->d_pblock, 0, 1, L->na, L->d_a, L->d_Pscale, L->d_q, 0, nullptr,
+                          (long long)(L->p_bytes / std::max(L->na, 1)), pdl, L->st));
+    else if (L->explicit_polc)
+        CK(L, launch_gemv(L->p_dtype, L->d_D, L->d_dblock, 0, 1, L->ns, L->d_a, L->d_Dscale, L->d_u, 0, nullptr,
+                          (long long)(L->p_bytes / std::max(L->ns, 1)), pdl, L->st));
+    return RTC_OK;
+}
+
 int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, const rtc_polc* P, rtc_loop* L) {
     if (!G || !M || !P) return fail(L, RTC_EINVAL, "geometry, cmat and polc are required");
     if (G->nwfs < 1 || G->nwfs > kMaxWfs || !G->wfs) return fail(L, RTC_EINVAL, "nwfs must be in [1, 16]");
@@ -316,6 +335,14 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
     if (M->dtype < RTC_F32 || M->dtype > RTC_E4M3 || !M->data || M->na < 1)
         return fail(L, RTC_EINVAL, "bad control matrix description");
     if (P->P && (P->dtype < RTC_F32 || P->dtype > RTC_E4M3)) return fail(L, RTC_EINVAL, "bad POLC dtype");
+    if (P->mode != RTC_POLC_IMPLICIT && P->mode != RTC_POLC_EXPLICIT) return fail(L, RTC_EINVAL, "bad POLC mode");
+    if (P->mode == RTC_POLC_EXPLICIT) {
+        if (P->P) return fail(L, RTC_EINVAL, "explicit POLC takes D, not P");
+        if (!P->D || P->d_dtype < RTC_F32 || P->d_dtype > RTC_E4M3)
+            return fail(L, RTC_EINVAL, "explicit POLC needs D with a valid d_dtype");
+    } else if (P->D) {
+        return fail(L, RTC_EINVAL, "D is only used in explicit POLC mode");
+    }
     if (!std::isfinite(P->gain) || !std::isfinite(P->leak)) return fail(L, RTC_EINVAL, "gain/leak not finite");
     if (P->clip && !(P->amin <= P->amax)) return fail(L, RTC_EINVAL, "clip needs amin <= amax");
 
@@ -330,7 +357,8 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
     L->nwfs = G->nwfs;
     L->na = M->na;
     L->m_dtype = M->dtype;
-    L->p_dtype = P->P ? P->dtype : RTC_F32;
+    L->explicit_polc = P->mode == RTC_POLC_EXPLICIT;
+    L->p_dtype = P->P ? P->dtype : L->explicit_polc ? P->d_dtype : RTC_F32;
     L->has_polc = P->P != nullptr;
     L->gain = P->gain;
     L->leak = P->leak;
@@ -379,8 +407,9 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
                 R.s_pad = x_off + local;
                 R.s_compact = compact + local;
                 rows.push_back(R);
+                const int qlast = *std::max_element(w.qy, w.qy + 4);
                 L->row_ready.push_back(sh ? w.oy + (i + 1) * w.npx
-                                          : *std::max_element(w.qy, w.qy + 4) + i + 1);
+                                          : qlast + (w.norm == RTC_NORM_GLOBAL ? w.pupil : i + 1));
                 xlist.insert(xlist.end(), row_x[i].begin(), row_x[i].end());
                 local += 2 * R.nunits;
             }
@@ -410,6 +439,13 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
         if (D.thresh_mode != RTC_THRESH_SUBTRACT && D.thresh_mode != RTC_THRESH_CLIP)
             return fail(L, RTC_EINVAL, "bad threshold mode");
         D.calib_pitch = (int)round_up((size_t)w.width, 4);
+        D.norm = sh ? RTC_NORM_LOCAL : w.norm;
+        D.grow0 = L->wfs_row0[k];
+        D.gnrows = nr;
+        D.gblk0 = L->wfs_blk0[k];
+        D.gnblk = w.nblocks;
+        D.gpix = 0;
+        for (int i = 0; i < nr; ++i) D.gpix += (int)row_x[i].size();
         if (sh) {
             const int ws = w.nsubx * w.npx;
             const int nq = ((w.ox + ws + 3) >> 2) - (w.ox >> 2);
@@ -455,6 +491,11 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
         }
     }
     L->part_start.push_back((int)parts.size());
+    for (int k = 0; k < L->nwfs; ++k)          // per-row flux sums of globally normalised pyramids
+        if (wdev[k].norm == RTC_NORM_GLOBAL) {
+            wdev[k].gflux = (int)pscr_floats;
+            pscr_floats += (size_t)wdev[k].gnrows;
+        }
     L->nfin = (L->na + kFinRows - 1) / kFinRows;
     L->ns = compact;
     if (M->ns != L->ns)
@@ -471,6 +512,8 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
     if (C && C->ref_slopes && !all_finite(C->ref_slopes, L->ns)) return fail(L, RTC_EINVAL, "ref_slopes not finite");
     if (M->row_scale && !all_finite(M->row_scale, L->na)) return fail(L, RTC_EINVAL, "row_scale not finite");
     if (P->P && P->row_scale && !all_finite(P->row_scale, L->na)) return fail(L, RTC_EINVAL, "P row_scale not finite");
+    if (P->D && P->d_row_scale && !all_finite(P->d_row_scale, L->ns))
+        return fail(L, RTC_EINVAL, "D row_scale not finite");
     if (P->a0 && !all_finite(P->a0, L->na)) return fail(L, RTC_EINVAL, "a0 not finite");
     for (int k = 0; k < L->nwfs; ++k) {
         const size_t n = (size_t)L->wfs[k].width * L->wfs[k].height;
@@ -481,6 +524,7 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
     // ---- HBM admission --------------------------------------------------
     size_t need = L->m_bytes + (size_t)L->na * M->ns * dtype_size(L->m_dtype);  // stored + upload temporary
     if (L->has_polc) need += (size_t)L->na * round_up(L->na, VP) * dtype_size(L->p_dtype) * 2;
+    if (L->explicit_polc) need += (size_t)L->ns * round_up(L->na, VP) * dtype_size(L->p_dtype) * 2 + (size_t)L->ns * 8;
     for (auto& w : L->wfs) need += (size_t)w.height * (round_up(w.width, 4) * 8 + round_up(w.width, 8) * 2);
     need += (size_t)L->nblk * L->na * 4 + (size_t)s_len * 4 + (size_t)a_len * 8;
     if (L->updatable) {
@@ -489,7 +533,8 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
         for (auto& w : L->wfs) need += (size_t)w.height * round_up(w.width, 4) * 8;
     }
     const size_t temporary = (size_t)L->na * M->ns * dtype_size(L->m_dtype) +
-                             (L->has_polc ? (size_t)L->na * round_up(L->na, VP) * dtype_size(L->p_dtype) : 0);
+                             (L->has_polc ? (size_t)L->na * round_up(L->na, VP) * dtype_size(L->p_dtype) : 0) +
+                             (L->explicit_polc ? (size_t)L->ns * round_up(L->na, VP) * dtype_size(L->p_dtype) : 0);
     L->need_peak = need;
     L->need_resident = need - temporary;
     if (L->plan_only) return RTC_OK;
@@ -543,6 +588,22 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
             TRY(dev_alloc(L, &L->d_Pscale, (size_t)L->na * 4));
             CK(L, cudaMemcpy(L->d_Pscale, P->row_scale, (size_t)L->na * 4, cudaMemcpyHostToDevice));
         }
+    }
+    if (L->explicit_polc) {
+        BlockDev DB{};
+        DB.ncols = L->na;
+        DB.pitch = (int)round_up((size_t)L->na, VP);
+        L->p_bytes = (uint64_t)L->ns * DB.pitch * dtype_size(L->p_dtype);
+        TRY(dev_alloc(L, &L->d_dblock, sizeof(BlockDev)));
+        CK(L, cudaMemcpy(L->d_dblock, &DB, sizeof(BlockDev), cudaMemcpyHostToDevice));
+        TRY(dev_alloc(L, &L->d_D, L->p_bytes));
+        TRY(upload_matrix(L, L->p_dtype, P->D, L->ns, L->na, L->d_dblock, std::vector<BlockDev>{DB}, L->d_D, true));
+        if (P->d_row_scale) {
+            TRY(dev_alloc(L, &L->d_Dscale, (size_t)L->ns * 4));
+            CK(L, cudaMemcpy(L->d_Dscale, P->d_row_scale, (size_t)L->ns * 4, cudaMemcpyHostToDevice));
+        }
+        TRY(dev_alloc(L, &L->d_u, (size_t)L->ns * 4));
+        CK(L, cudaMemset(L->d_u, 0, (size_t)L->ns * 4));
     }
     // calibration maps and frame buffers
     L->d_dark.resize(L->nwfs);
@@ -631,10 +692,7 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
     if (P->a0) CK(L, cudaMemcpy(L->d_a, P->a0, (size_t)L->na * 4, cudaMemcpyHostToDevice));
     TRY(dev_alloc(L, &L->d_q, (size_t)L->na * 4));
     CK(L, cudaMemset(L->d_q, 0, (size_t)L->na * 4));
-    if (L->has_polc) {
-        CK(L, launch_gemv(L->p_dtype, L->d_P, L->d_pblock, 0, 1, L->na, L->d_a, L->d_Pscale, L->d_q, 0, nullptr,
-                          (long long)(L->p_bytes / std::max(L->na, 1)), false, L->st));
-    }
+    TRY(polc_product(L, false));
 
     // ---- page-locked ring, events -------------------------------------------
     L->slot_floats = round_up((size_t)L->na, 4) + round_up((size_t)L->ns, 4);
@@ -772,9 +830,7 @@ int enqueue_tail(rtc_loop* L) {
     Slot& s = L->slots[L->cur_slot];
     float* cmd = L->d_ring + (size_t)L->cur_slot * L->slot_floats;
     if (L->timing) TRY(record(L, s.ev_final, L->st));
-    if (L->has_polc)
-        CK(L, launch_gemv(L->p_dtype, L->d_P, L->d_pblock, 0, 1, L->na, L->d_a, L->d_Pscale, L->d_q, 0, nullptr,
-                          (long long)(L->p_bytes / std::max(L->na, 1)), !L->timing, L->st));
+    TRY(polc_product(L, !L->timing));
     TRY(record(L, s.ev_polc, L->st));
     if (L->telemetry) {
         CK(L, cudaStreamWaitEvent(L->st_tel, s.ev_polc, 0));
@@ -829,7 +885,7 @@ FinaliseArgs fin_args(rtc_loop* L) {
     f.q = L->d_q;
     f.a = L->d_a;
     f.cmd = L->d_ring + (size_t)L->cur_slot * L->slot_floats;
-    f.oml = 1.0f - L->leak;
+    f.oml = L->explicit_polc ? 1.0f - L->leak - L->gain : 1.0f - L->leak;
     f.gain = L->gain;
     f.clip = L->clip;
     f.amin = L->amin;
@@ -842,8 +898,8 @@ FinaliseArgs fin_args(rtc_loop* L) {
 
 int slopes_rows(rtc_loop* L, int r0, int r1, const FramePtrs& fp, cudaStream_t st) {
     const int p0 = L->part_start[r0], p1 = L->part_start[r1];
-    CK(L, launch_slopes(L->d_parts, p0, p1 - p0, L->d_rows, L->d_wfs, fp, L->d_xlist, L->d_ref, L->d_s, L->d_pscr,
-                        L->d_row_cnt, L->smem_bytes, st));
+    CK(L, launch_slopes(L->d_parts, p0, p1 - p0, L->d_rows, L->d_wfs, L->d_blocks, fp, L->d_xlist, L->d_ref,
+                        L->explicit_polc ? L->d_u : nullptr, L->d_s, L->d_pscr, L->d_row_cnt, L->smem_bytes, st));
     return RTC_OK;
 }
 
@@ -1307,7 +1363,9 @@ int rtc_get_timing(rtc_loop* L, uint64_t frame_id, rtc_timing* out, int64_t time
 int rtc_update(rtc_loop* L, const rtc_update_desc* d) {
     if (!L || !d) return fail(L, RTC_EINVAL, "loop and desc are required");
     if (!L->updatable) return fail(L, RTC_EINVAL, "loop created without RTC_FLAG_UPDATABLE");
-    if ((d->P || d->P_scale) && !L->has_polc) return fail(L, RTC_EINVAL, "loop has no POLC matrix");
+    if ((d->P || d->P_scale) && !L->has_polc)
+        return fail(L, RTC_EINVAL, L->explicit_polc ? "an explicit-POLC loop's D is fixed at creation"
+                                                    : "loop has no POLC matrix");
     if (d->M_scale && !L->d_Mscale) return fail(L, RTC_EINVAL, "loop was created without control-matrix row scales");
     if (d->P_scale && !L->d_Pscale) return fail(L, RTC_EINVAL, "loop was created without POLC row scales");
     // validate everything before touching any buffer
@@ -1422,9 +1480,7 @@ int rtc_set_state(rtc_loop* L, const float* a, size_t na) {
     for (cudaStream_t w : L->st_w) CK(L, cudaStreamSynchronize(w));
     CK(L, cudaStreamSynchronize(L->st));
     CK(L, cudaMemcpy(L->d_a, a, na * 4, cudaMemcpyHostToDevice));
-    if (L->has_polc)
-        CK(L, launch_gemv(L->p_dtype, L->d_P, L->d_pblock, 0, 1, L->na, L->d_a, L->d_Pscale, L->d_q, 0, nullptr,
-                          (long long)(L->p_bytes / std::max(L->na, 1)), false, L->st));
+    TRY(polc_product(L, false));
     CK(L, cudaStreamSynchronize(L->st));
     return RTC_OK;
 }

@@ -39,7 +39,8 @@ struct OwnedDesc {
     std::vector<const float*> dark_p, flat_p;
     std::vector<float> threshold, ref, Ms, Ps, a0;
     std::vector<int32_t> mode;
-    std::vector<uint8_t> M, P;
+    std::vector<uint8_t> M, P, D;
+    std::vector<float> Ds;
     rtc_geometry g{};
     rtc_calib c{};
     rtc_cmat m{};
@@ -72,6 +73,11 @@ struct OwnedDesc {
             P.assign(static_cast<const uint8_t*>(Px->P), static_cast<const uint8_t*>(Px->P) + pb);
             if (Px->row_scale) Ps.assign(Px->row_scale, Px->row_scale + Mx->na);
         }
+        if (Px->D) {
+            const size_t db = (size_t)Mx->ns * Mx->na * esize(Px->d_dtype);
+            D.assign(static_cast<const uint8_t*>(Px->D), static_cast<const uint8_t*>(Px->D) + db);
+            if (Px->d_row_scale) Ds.assign(Px->d_row_scale, Px->d_row_scale + Mx->ns);
+        }
         if (Px->a0) a0.assign(Px->a0, Px->a0 + Mx->na);
         // pointers into the copies
         for (int k = 0; k < G->nwfs; ++k) wfs[k].valid = valid[k].empty() ? nullptr : valid[k].data();
@@ -92,6 +98,8 @@ struct OwnedDesc {
         p.P = P.empty() ? nullptr : P.data();
         p.row_scale = Ps.empty() ? nullptr : Ps.data();
         p.a0 = a0.empty() ? nullptr : a0.data();
+        p.D = D.empty() ? nullptr : D.data();
+        p.d_row_scale = Ds.empty() ? nullptr : Ds.data();
     }
 };
 

@@ -121,6 +121,15 @@ def polc_matrix(rng, na, rel_sd=0.2):
     return p
 
 
+def interaction_matrix(rng, ns, na, m_sd=1e-3, radius=0.2):
+    """Interaction matrix D, float32 [ns, na], entries N(0, sd^2) with
+    sd = radius / (m_sd * sqrt(na * ns)): with a control matrix of N(0, m_sd^2)
+    entries, M*D then has spectral radius about `radius`, so the explicit POLC
+    iteration (1 - leak - g) I + g M D stays well inside the unit circle."""
+    sd = radius / (m_sd * math.sqrt(float(na) * float(ns)))
+    return rng.standard_normal((ns, na), dtype=np.float32) * np.float32(sd)
+
+
 def make_config(name: str, seed: int | None = None, *, polc=None, gain=0.5,
                 leak=0.01, clip=None, with_ref=False, nblocks=None):
     """Build one of the named configurations with its seeded arrays.

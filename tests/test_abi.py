@@ -39,7 +39,7 @@ def test_create_rejects_null_and_bad_geometry_without_gpu(rtc):
     w[0].npx, w[0].nblocks = 8, 1          # 3 x 8 = 24 > 16: grid outside the frame
     geo = rtc.rtc_geometry(1, w, 0, 0, 4)
     cm = rtc.rtc_cmat(1, 18, rtc.RTC_F32, C.c_void_p(1), None)
-    pol = rtc.rtc_polc(None, 0, None, 0.5, 0.01, None, 0, 0.0, 0.0)
+    pol = rtc.rtc_polc(None, 0, None, 0.5, 0.01, None, 0, 0.0, 0.0, 0, None, 0, None)
     assert rtc.lib.rtc_create(C.byref(geo), None, C.byref(cm), C.byref(pol), C.byref(h)) == rtc.RTC_EINVAL
     assert b"outside the frame" in rtc.lib.rtc_last_error(None)
     w[0].npx, w[0].nblocks = 4, 5          # more blocks than subaperture rows
@@ -76,3 +76,75 @@ def test_footprint_is_computed_without_gpu_and_scales_with_storage(rtc):
     import pytest
     with pytest.raises(rtc.RtcError):
         rtc.footprint(bad)
+
+
+def test_structs_mirror_the_header_layout(rtc, tmp_path):
+    """Every ctypes struct of the binding has the size and field offsets the C
+    compiler gives the header's struct (checked with gcc on this host)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    structs = [rtc.rtc_wfs, rtc.rtc_geometry, rtc.rtc_calib, rtc.rtc_cmat, rtc.rtc_polc, rtc.rtc_chunk,
+               rtc.rtc_timing, rtc.rtc_update_desc, rtc.rtc_server_loop_info, rtc.rtc_info]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "rtc.h"', "int main(void) {"]
+    for st in structs:
+        n = st.__name__
+        lines.append(f'printf("{n} %zu\\n", sizeof({n}));')
+        for f, _ in st._fields_:
+            lines.append(f'printf("{n}.{f} %zu\\n", offsetof({n}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                 text=True).stdout.splitlines())
+    for st in structs:
+        n = st.__name__
+        assert int(got[n]) == C.sizeof(st), n
+        for f, _ in st._fields_:
+            assert int(got[f"{n}.{f}"]) == getattr(st, f).offset, f"{n}.{f}"
+
+
+def test_explicit_polc_and_norm_validation_without_gpu(rtc):
+    import numpy as np
+    from paper_1903_01852_gb300 import synth
+    cfg = synth.make_config("scao_small")
+    na, ns = cfg["na"], cfg["ns"]
+    D = np.zeros((ns, na), np.float32)
+    base = dict(cfg, P=None)
+    r0, _ = rtc.footprint(base)
+    r1, p1 = rtc.footprint(dict(base, polc="explicit", D=D))
+    assert r1 - r0 >= ns * na * 4 and p1 > r1                 # D is resident, and uploaded through a temporary
+    r, p = C.c_uint64(), C.c_uint64()
+    P = np.zeros((na, na), np.float32)
+    st = rtc.describe(dict(base, polc="explicit", D=D))
+    st.pol.P = P.ctypes.data                                  # explicit mode with a P as well
+    assert rtc.lib.rtc_footprint(C.byref(st.geo), C.byref(st.cal), C.byref(st.cm), C.byref(st.pol), C.byref(r),
+                                 C.byref(p)) == rtc.RTC_EINVAL
+    assert b"takes D, not P" in rtc.lib.rtc_last_error(None)
+    st.pol.P = None
+    st.pol.D = None
+    assert rtc.lib.rtc_footprint(C.byref(st.geo), C.byref(st.cal), C.byref(st.cm), C.byref(st.pol), C.byref(r),
+                                 C.byref(p)) == rtc.RTC_EINVAL
+    assert b"needs D" in rtc.lib.rtc_last_error(None)
+    st = rtc.describe(base)
+    st.pol.D = D.ctypes.data                                  # D without explicit mode
+    assert rtc.lib.rtc_footprint(C.byref(st.geo), C.byref(st.cal), C.byref(st.cm), C.byref(st.pol), C.byref(r),
+                                 C.byref(p)) == rtc.RTC_EINVAL
+    st = rtc.describe(base)
+    st.pol.mode = 7
+    assert rtc.lib.rtc_footprint(C.byref(st.geo), C.byref(st.cal), C.byref(st.cm), C.byref(st.pol), C.byref(r),
+                                 C.byref(p)) == rtc.RTC_EINVAL
+    st = rtc.describe(base)
+    st.geo.wfs[0].norm = rtc.RTC_NORM_GLOBAL                  # SH WFS: no normalisation choice
+    assert rtc.lib.rtc_footprint(C.byref(st.geo), C.byref(st.cal), C.byref(st.cm), C.byref(st.pol), C.byref(r),
+                                 C.byref(p)) == rtc.RTC_EINVAL
+    assert b"pyramid WFS only" in rtc.lib.rtc_last_error(None)
+    pyr = synth.make_config("elt_scao_pyramid")
+    assert rtc.footprint(dict(pyr, wfs=[dict(pyr["wfs"][0], norm="global")]))[0] > 0
+    st = rtc.describe(pyr)
+    st.geo.wfs[0].norm = 2
+    assert rtc.lib.rtc_footprint(C.byref(st.geo), C.byref(st.cal), C.byref(st.cm), C.byref(st.pol), C.byref(r),
+                                 C.byref(p)) == rtc.RTC_EINVAL
