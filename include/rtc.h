@@ -81,6 +81,13 @@ extern "C" {
 
 #define RTC_MAX_WFS 16
 
+/* Sections of a telemetry circular-buffer entry (rtc_geometry.tel_streams). */
+#define RTC_TEL_SLOPES   1u /* the frame's slopes (ns floats; POL slopes in explicit-POLC mode) */
+#define RTC_TEL_COMMANDS 2u /* the frame's commands (na floats) */
+#define RTC_TEL_PARTIALS 4u /* per-WFS partial commands: nwfs x na floats, the reconstruction of
+                               each WFS's slopes alone (what the paper's reconstruction nodes
+                               send to the master, Section 3), before POLC and the integrator */
+
 /* ---- creation-time descriptions ------------------------------------- */
 
 /* One wavefront sensor.  Pixel frames are uint16, row-major, height x width.
@@ -112,13 +119,23 @@ typedef struct rtc_wfs {
     int32_t norm;                        /* RTC_NORM_* (pyramid only) */
 } rtc_wfs;
 
-/* The loop's sensors and run-time options. */
+/* The loop's sensors and run-time options.
+ * tel_depth > 0 adds a telemetry circular buffer (Section 3.3: DARC keeps
+ * telemetry in circular buffers that readers drain while the loop runs) of
+ * tel_depth entries in page-locked host memory, written by the GPU after each
+ * recorded frame's commands, off the latency path.  Every tel_decimate-th
+ * frame that completes is recorded (tel_decimate >= 1), with the sections
+ * tel_streams (RTC_TEL_*, may be 0 for timing records only).  Read it with
+ * rtc_telemetry_read.  0 <= tel_depth <= 1 << 20. */
 typedef struct rtc_geometry {
     int32_t nwfs;                /* 1..RTC_MAX_WFS */
     const rtc_wfs* wfs;          /* host array of nwfs */
     int32_t device;              /* CUDA device ordinal */
     uint32_t flags;              /* RTC_FLAG_* */
     int32_t ring;                /* depth of the page-locked command/telemetry ring, >= 2 */
+    int32_t tel_depth;           /* telemetry circular-buffer entries, 0 for none */
+    uint32_t tel_streams;        /* RTC_TEL_* */
+    int32_t tel_decimate;        /* record every n-th frame (0 is taken as 1) */
 } rtc_geometry;
 
 /* Pixel calibration (Section 2.2): c = (raw - dark) * flat, then the threshold.
@@ -277,6 +294,32 @@ typedef struct rtc_timing {
     float latency_us, frame_us;  /* frame_us: first submitted work to end of finalise */
 } rtc_timing;
 int rtc_get_timing(rtc_loop* loop, uint64_t frame_id, rtc_timing* out, int64_t timeout_us);
+
+/* ---- telemetry circular buffer (Section 3.3) ------------------------------ */
+
+/* One entry's record.  Times are the GPU's global timer in nanoseconds, so
+ * differences between records are device frame times. */
+typedef struct rtc_tel_record {
+    uint64_t index;              /* entry number: 0, 1, 2, ... over recorded frames */
+    uint64_t frame_id;
+    uint64_t t_commands_ns;      /* when the frame's commands were complete */
+    uint64_t t_written_ns;       /* when the entry was written */
+    uint64_t lost;               /* entries overwritten before this reader reached them, since the
+                                    previous successful read */
+} rtc_tel_record;
+
+/* The oldest entry not yet read, waiting up to timeout_us (< 0: forever) for
+ * one to be published.  A reader that falls more than tel_depth - 1 entries
+ * behind loses the oldest ones (counted in rec->lost), as with DARC's circular
+ * buffers; an entry that the GPU may have been rewriting while it was copied is
+ * also counted lost.  slopes (ns floats), cmds (na floats) and partials
+ * (nwfs x na floats, row-major by WFS) receive the recorded sections and may
+ * be NULL; a non-NULL pointer for a section the loop does not record, or a
+ * wrong size, is RTC_EINVAL.  One reader at a time per loop (calls are
+ * serialised).  RTC_ETIMEDOUT when nothing new was published in time;
+ * RTC_EINVAL when the loop has no telemetry buffer. */
+int rtc_telemetry_read(rtc_loop* loop, rtc_tel_record* rec, float* slopes, size_t ns, float* cmds, size_t na,
+                       float* partials, size_t npartials, int64_t timeout_us);
 
 /* ---- parameter double buffer (Section 3.2) ----------------------------- */
 

@@ -26,6 +26,7 @@ RTC_NORM_LOCAL, RTC_NORM_GLOBAL = 0, 1
 RTC_POLC_IMPLICIT, RTC_POLC_EXPLICIT = 0, 1
 RTC_FLAG_TIMING, RTC_FLAG_TELEMETRY, RTC_FLAG_STAGE_TIMING, RTC_FLAG_UPDATABLE, RTC_FLAG_GRAPHS = 1, 2, 4, 8, 16
 RTC_MAX_WFS = 16
+RTC_TEL_SLOPES, RTC_TEL_COMMANDS, RTC_TEL_PARTIALS = 1, 2, 4
 DTYPES = {"f32": RTC_F32, "bf16": RTC_BF16, "e4m3": RTC_E4M3}
 CODE_NP = {RTC_F32: np.float32, RTC_BF16: np.uint16, RTC_E4M3: np.uint8}
 STATUS = {0: "RTC_OK", -1: "RTC_EINVAL", -2: "RTC_ENOMEM", -3: "RTC_ETIMEDOUT", -4: "RTC_EORDER",
@@ -43,7 +44,8 @@ class rtc_wfs(C.Structure):
 
 class rtc_geometry(C.Structure):
     _fields_ = [("nwfs", C.c_int32), ("wfs", C.POINTER(rtc_wfs)), ("device", C.c_int32),
-                ("flags", C.c_uint32), ("ring", C.c_int32)]
+                ("flags", C.c_uint32), ("ring", C.c_int32), ("tel_depth", C.c_int32), ("tel_streams", C.c_uint32),
+                ("tel_decimate", C.c_int32)]
 
 
 class rtc_calib(C.Structure):
@@ -72,6 +74,11 @@ class rtc_timing(C.Structure):
     _fields_ = [("frame_id", C.c_uint64), ("slopes_us", C.c_float), ("mvm_us", C.c_float),
                 ("final_us", C.c_float), ("polc_us", C.c_float), ("latency_us", C.c_float),
                 ("frame_us", C.c_float)]
+
+
+class rtc_tel_record(C.Structure):
+    _fields_ = [("index", C.c_uint64), ("frame_id", C.c_uint64), ("t_commands_ns", C.c_uint64),
+                ("t_written_ns", C.c_uint64), ("lost", C.c_uint64)]
 
 
 class rtc_update_desc(C.Structure):
@@ -107,6 +114,8 @@ SIGNATURES = [
     ("rtc_get_commands", C.c_int, [C.c_void_p, f32p, C.c_size_t, C.POINTER(C.c_uint64), C.c_int64]),
     ("rtc_get_telemetry", C.c_int, [C.c_void_p, C.c_uint64, f32p, C.c_size_t, f32p, C.c_size_t, C.c_int64]),
     ("rtc_get_timing", C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(rtc_timing), C.c_int64]),
+    ("rtc_telemetry_read", C.c_int, [C.c_void_p, C.POINTER(rtc_tel_record), f32p, C.c_size_t, f32p, C.c_size_t,
+                                     f32p, C.c_size_t, C.c_int64]),
     ("rtc_update", C.c_int, [C.c_void_p, C.POINTER(rtc_update_desc)]),
     ("rtc_get_state", C.c_int, [C.c_void_p, f32p, C.c_size_t]),
     ("rtc_set_state", C.c_int, [C.c_void_p, f32p, C.c_size_t]),
@@ -190,8 +199,9 @@ class _Described:
     """The C structs of one loop description, and the arrays they point into."""
 
 
-def describe(cfg, device=0, flags=0, ring=4):
-    """Build rtc_geometry / rtc_calib / rtc_cmat / rtc_polc from a configuration dict."""
+def describe(cfg, device=0, flags=0, ring=4, tel=(0, 0, 1)):
+    """Build rtc_geometry / rtc_calib / rtc_cmat / rtc_polc from a configuration dict.
+    tel: (depth, RTC_TEL_* streams, decimate) of the telemetry circular buffer."""
     wl = cfg["wfs"]
     if len(wl) > RTC_MAX_WFS:
         raise ValueError("too many WFS")
@@ -222,7 +232,7 @@ def describe(cfg, device=0, flags=0, ring=4):
         keep += [d, f]
         darks[k] = _fptr(d)
         flats[k] = _fptr(f)
-    st.geo = rtc_geometry(len(wl), warr, device, flags, ring)
+    st.geo = rtc_geometry(len(wl), warr, device, flags, ring, int(tel[0]), int(tel[1]), int(tel[2]))
     ref = _f32(cfg.get("ref_slopes"))
     st.cal = rtc_calib(darks, flats, thr.ctypes.data_as(f32p), mode.ctypes.data_as(C.POINTER(C.c_int32)), _fptr(ref))
     mdt = DTYPES[cfg.get("M_dtype", "f32")]
@@ -262,7 +272,8 @@ class Loop:
     """One AO loop on one GPU, built from a configuration dict (see synth)."""
 
     def __init__(self, cfg, device=0, timing=False, telemetry=False, ring=4, stage_timing=False, updatable=False,
-                 graphs=False, _handle=None):
+                 graphs=False, tel_depth=0, tel_streams=RTC_TEL_SLOPES | RTC_TEL_COMMANDS, tel_decimate=1,
+                 _handle=None):
         self.cfg = cfg
         self.na = int(cfg["na"])
         self._owned = _handle is None
@@ -270,7 +281,7 @@ class Loop:
             flags = ((RTC_FLAG_TIMING if timing or stage_timing else 0) | (RTC_FLAG_TELEMETRY if telemetry else 0)
                      | (RTC_FLAG_STAGE_TIMING if stage_timing else 0) | (RTC_FLAG_UPDATABLE if updatable else 0)
                      | (RTC_FLAG_GRAPHS if graphs else 0))
-            st = describe(cfg, device, flags, ring)
+            st = describe(cfg, device, flags, ring, (tel_depth, tel_streams, tel_decimate))
             h = C.c_void_p()
             _check(lib.rtc_create(C.byref(st.geo), C.byref(st.cal), C.byref(st.cm), C.byref(st.pol), C.byref(h)))
             self._h = h
@@ -359,6 +370,20 @@ class Loop:
         _check(lib.rtc_get_telemetry(self._h, frame_id, s.ctypes.data_as(f32p), self.ns,
                                      a.ctypes.data_as(f32p), self.na, int(timeout_us)), self._h)
         return s, a
+
+    def telemetry_read(self, timeout_us=-1, slopes=True, cmds=True, partials=False):
+        """rtc_telemetry_read: the oldest unread entry of the telemetry circular buffer, as
+        (record dict, slopes, commands, partials [nwfs, na]); sections not asked for are None."""
+        nw = len(self.cfg["wfs"])
+        s = np.empty(self.ns, np.float32) if slopes else None
+        a = np.empty(self.na, np.float32) if cmds else None
+        p = np.empty((nw, self.na), np.float32) if partials else None
+        r = rtc_tel_record()
+        ptr = lambda x: None if x is None else x.ctypes.data_as(f32p)
+        _check(lib.rtc_telemetry_read(self._h, C.byref(r), ptr(s), self.ns if slopes else 0, ptr(a),
+                                      self.na if cmds else 0, ptr(p), nw * self.na if partials else 0,
+                                      int(timeout_us)), self._h)
+        return {k: getattr(r, k) for k, _ in rtc_tel_record._fields_}, s, a, p
 
     def get_timing(self, frame_id, timeout_us=-1):
         t = rtc_timing()

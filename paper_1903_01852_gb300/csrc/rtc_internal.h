@@ -72,6 +72,8 @@ struct FinaliseArgs {
     unsigned long long* done_flag;  // page-locked completion word of the ring slot, or NULL
     const unsigned long long* seq;  // page-locked word holding the value to write there (set by the
                                     // host before the launch, so a captured graph can be replayed)
+    unsigned long long* t_done;     // device word of the slot: GPU global time (ns) when the commands
+                                    // were complete, or NULL
 };
 
 // Frame pointers for one launch; pitch in uint16 elements.  px[w] holds pixel
@@ -96,6 +98,37 @@ int elems_per_16B(int dtype);
 
 // Opt the slope kernel in to more than 48 KB of dynamic shared memory when needed.
 cudaError_t configure_slopes(int smem_bytes);
+
+// Telemetry circular buffer (Section 3.3): one entry per recorded frame, in
+// page-locked host memory written by the GPU.  An entry is a header of
+// kTelHeaderFloats floats (TelHeader) and then the recorded sections.
+constexpr int kTelHeaderFloats = 16;
+struct TelHeader {
+    unsigned long long index;       // entry number
+    unsigned long long frame_id;
+    unsigned long long t_commands;  // GPU global time (ns): commands complete
+    unsigned long long t_written;   // GPU global time (ns): entry written
+};
+struct TelArgs {
+    const BlockDev* blocks;
+    int nblk, na, ns, nwfs;
+    int blk_start[kMaxWfs + 1];     // column blocks of WFS w: [blk_start[w], blk_start[w + 1])
+    const float* s_pad;             // slopes, padded block layout
+    const float* a;                 // commands
+    const float* part;              // unscaled per-block partial products, [nblk][na]
+    const float* scale;             // control-matrix row scales or NULL
+    unsigned streams;               // RTC_TEL_* sections recorded
+    int off_s, off_a, off_p;        // float offsets of the sections after the header
+    int decimate;                   // record every decimate-th frame that reaches telemetry
+    long long depth;                // entries in the ring
+    long long entry_floats;         // entry stride
+    float* ring;                    // page-locked entries (device address)
+    unsigned long long* wcount;     // page-locked: entries published so far
+    unsigned long long* ctr;        // device: [0] frames seen, [1] entries written, [2] CTAs finished
+    const unsigned long long* fid;  // page-locked: frame id of the slot
+    const unsigned long long* t_cmd;  // device: the slot's command-complete time
+};
+cudaError_t launch_telemetry(const TelArgs& t, cudaStream_t st);
 
 // Slope kernel over the part table entries [part0, part0 + nparts).  Each slope
 // is (measured - ref) + pol, with ref and pol (compact slope order) optional;

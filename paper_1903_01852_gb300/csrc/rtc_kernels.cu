@@ -34,6 +34,13 @@ __device__ __forceinline__ float warp_sum(float v) {
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// GPU global timer in nanoseconds.
+__device__ __forceinline__ unsigned long long global_time_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Bulk prefetch of a contiguous, 16-byte aligned region into L2 (TMA engine).
 __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
@@ -554,12 +561,84 @@ __global__ void __launch_bounds__(kGemvWarps * 32) gemv_kernel(const __grid_cons
             const int nfin = (a.na + kFinRows - 1) / kFinRows;
             if (atomicAdd(a.fin.tiles_done, 1u) == (unsigned)(nfin - 1)) {
                 *a.fin.tiles_done = 0u;
+                if (a.fin.t_done) *a.fin.t_done = global_time_ns();
                 __threadfence_system();
                 const unsigned long long seq = *reinterpret_cast<const volatile unsigned long long*>(a.fin.seq);
                 *reinterpret_cast<volatile unsigned long long*>(a.fin.done_flag) = seq;
             }
         }
     }
+}
+
+// Telemetry entry of one frame: grid.y enumerates the recorded sections (one
+// slope block per y, then the commands, then one WFS's partial commands per y),
+// grid.x splits each section.  Every CTA reads the frame and entry counters
+// when it starts; the last CTA to finish publishes the entry (header, then the
+// published count, after a system-scope fence) and advances the counters, so
+// the next launch (stream-ordered) sees them.
+__global__ void __launch_bounds__(256) telemetry_kernel(const __grid_constant__ TelArgs t) {
+    __shared__ int s_last;
+    const unsigned long long frame = t.ctr[0];
+    const unsigned long long idx = t.ctr[1];
+    const bool rec = frame % (unsigned long long)t.decimate == 0ull;
+    if (rec) {
+        float* e = t.ring + (long long)(idx % (unsigned long long)t.depth) * t.entry_floats + kTelHeaderFloats;
+        const int stride = gridDim.x * blockDim.x;
+        const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+        int sec = blockIdx.y;
+        if (t.streams & RTC_TEL_SLOPES) {
+            if (sec < t.nblk) {
+                const BlockDev B = t.blocks[sec];
+                for (int j = i0; j < B.ncols; j += stride) e[t.off_s + B.c0 + j] = t.s_pad[B.x_off + j];
+            }
+            sec -= t.nblk;
+        }
+        if (t.streams & RTC_TEL_COMMANDS) {
+            if (sec == 0)
+                for (int r = i0; r < t.na; r += stride) e[t.off_a + r] = t.a[r];
+            sec -= 1;
+        }
+        if ((t.streams & RTC_TEL_PARTIALS) && sec >= 0 && sec < t.nwfs) {
+            const int b0 = t.blk_start[sec], b1 = t.blk_start[sec + 1];
+            for (int r = i0; r < t.na; r += stride) {
+                float y = 0.f;
+                for (int b = b0; b < b1; ++b) y += t.part[(size_t)b * t.na + r];
+                if (t.scale) y *= t.scale[r];
+                e[t.off_p + (size_t)sec * t.na + r] = y;
+            }
+        }
+    }
+    __threadfence_system();
+    __syncthreads();
+    if (threadIdx.x == 0)
+        s_last = atomicAdd(&t.ctr[2], 1ull) == (unsigned long long)(gridDim.x * gridDim.y) - 1ull;
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return;
+    __threadfence();
+    if (rec) {
+        TelHeader* h = reinterpret_cast<TelHeader*>(t.ring + (long long)(idx % (unsigned long long)t.depth) *
+                                                                 t.entry_floats);
+        h->index = idx;
+        h->frame_id = *reinterpret_cast<const volatile unsigned long long*>(t.fid);
+        h->t_commands = *t.t_cmd;
+        h->t_written = global_time_ns();
+        __threadfence_system();
+        *reinterpret_cast<volatile unsigned long long*>(t.wcount) = idx + 1ull;
+        t.ctr[1] = idx + 1ull;
+    }
+    t.ctr[0] = frame + 1ull;
+    t.ctr[2] = 0ull;
+    __threadfence_system();
+}
+
+cudaError_t launch_telemetry(const TelArgs& t, cudaStream_t st) {
+    int ny = 0;
+    if (t.streams & RTC_TEL_SLOPES) ny += t.nblk;
+    if (t.streams & RTC_TEL_COMMANDS) ny += 1;
+    if (t.streams & RTC_TEL_PARTIALS) ny += t.nwfs;
+    const dim3 grid(4, (unsigned)std::max(ny, 1));
+    telemetry_kernel<<<grid, 256, 0, st>>>(t);
+    return cudaGetLastError();
 }
 
 template <typename K>

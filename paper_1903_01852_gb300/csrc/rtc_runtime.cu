@@ -10,6 +10,7 @@
 #include <deque>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "rtc_internal.h"
@@ -95,6 +96,9 @@ struct rtc_loop {
     unsigned long long* d_done = nullptr;
     unsigned long long* h_seq = nullptr;    // per slot: the value its frame writes to h_done (host-set)
     unsigned long long* d_seq = nullptr;
+    unsigned long long* h_fid = nullptr;    // per slot: its frame id (host-set, read by the telemetry kernel)
+    unsigned long long* d_fid = nullptr;
+    unsigned long long* d_tdone = nullptr;  // per slot: GPU time its commands were complete (device)
     unsigned* d_tiles_done = nullptr;
     uint64_t frame_seq = 0;
     size_t slot_floats = 0;
@@ -150,6 +154,20 @@ struct rtc_loop {
     bool cuda_touched = false;   // false until creation first calls into CUDA
     bool plan_only = false;      // rtc_footprint: stop after planning, before any CUDA call
     uint64_t need_resident = 0, need_peak = 0;
+
+    // telemetry circular buffer (tel_depth > 0): entries in page-locked memory written by the GPU
+    long long tel_depth = 0;
+    unsigned tel_streams = 0;
+    int tel_decimate = 1;
+    long long tel_entry_floats = 0;
+    int tel_off_s = 0, tel_off_a = 0, tel_off_p = 0;
+    float* h_tel = nullptr;
+    float* d_tel = nullptr;
+    unsigned long long* h_wcount = nullptr;   // entries published (page-locked, GPU-written)
+    unsigned long long* d_wcount = nullptr;
+    unsigned long long* d_telctr = nullptr;   // device counters of the telemetry kernel
+    std::mutex tel_mu;                        // one reader at a time
+    uint64_t tel_next = 0, tel_lost = 0;
 
     // graph mode (RTC_FLAG_GRAPHS): per ring slot, page-locked input frames and a captured frame graph
     bool graphs = false;
@@ -245,6 +263,7 @@ void release(rtc_loop* L) {
     for (void* p : L->allocs) cudaFree(p);
     if (L->h_ring) cudaFreeHost(L->h_ring);
     if (L->h_done) cudaFreeHost(L->h_done);
+    if (L->h_tel) cudaFreeHost(L->h_tel);
     if (L->st_up) cudaStreamSynchronize(L->st_up);
     if (L->ev_swap) cudaEventDestroy(L->ev_swap);
     if (L->st) cudaStreamDestroy(L->st);
@@ -366,6 +385,13 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
     L->amin = P->amin;
     L->amax = P->amax;
     L->graphs = (G->flags & RTC_FLAG_GRAPHS) != 0;
+    if (G->tel_depth < 0 || G->tel_depth > (1 << 20)) return fail(L, RTC_EINVAL, "tel_depth must be in [0, 2^20]");
+    if (G->tel_decimate < 0) return fail(L, RTC_EINVAL, "tel_decimate must be >= 0");
+    if (G->tel_streams & ~(RTC_TEL_SLOPES | RTC_TEL_COMMANDS | RTC_TEL_PARTIALS))
+        return fail(L, RTC_EINVAL, "unknown tel_streams bits");
+    L->tel_depth = G->tel_depth;
+    L->tel_streams = G->tel_depth ? G->tel_streams : 0u;
+    L->tel_decimate = G->tel_decimate > 0 ? G->tel_decimate : 1;
     if (L->graphs && L->updatable) return fail(L, RTC_EINVAL, "RTC_FLAG_GRAPHS and RTC_FLAG_UPDATABLE exclude each other");
 
     // ---- slope-row and block plans ------------------------------------
@@ -711,18 +737,47 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
     }
     {
         void* h = nullptr;
-        cudaError_t e = cudaHostAlloc(&h, 2 * (size_t)L->ring * sizeof(unsigned long long), cudaHostAllocMapped);
+        // per slot: completion word, its expected value, frame id; then the telemetry count
+        const size_t words = 3 * (size_t)L->ring + 1;
+        cudaError_t e = cudaHostAlloc(&h, words * sizeof(unsigned long long), cudaHostAllocMapped);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return fail(L, RTC_ENOMEM, "page-locked completion words");
         }
         L->h_done = static_cast<unsigned long long*>(h);
         L->h_seq = L->h_done + L->ring;
-        std::memset(h, 0, 2 * (size_t)L->ring * sizeof(unsigned long long));
+        L->h_fid = L->h_seq + L->ring;
+        L->h_wcount = L->h_fid + L->ring;
+        std::memset(h, 0, words * sizeof(unsigned long long));
         void* d = nullptr;
         CK(L, cudaHostGetDevicePointer(&d, h, 0));
         L->d_done = static_cast<unsigned long long*>(d);
         L->d_seq = L->d_done + L->ring;
+        L->d_fid = L->d_seq + L->ring;
+        L->d_wcount = L->d_fid + L->ring;
+    }
+    TRY(dev_alloc(L, &L->d_tdone, (size_t)L->ring * sizeof(unsigned long long)));
+    CK(L, cudaMemset(L->d_tdone, 0, (size_t)L->ring * sizeof(unsigned long long)));
+    if (L->tel_depth) {
+        auto r4 = [](long long n) { return (n + 3) / 4 * 4; };
+        long long off = 0;
+        if (L->tel_streams & RTC_TEL_SLOPES) { L->tel_off_s = (int)off; off += r4(L->ns); }
+        if (L->tel_streams & RTC_TEL_COMMANDS) { L->tel_off_a = (int)off; off += r4(L->na); }
+        if (L->tel_streams & RTC_TEL_PARTIALS) { L->tel_off_p = (int)off; off += r4((long long)L->nwfs * L->na); }
+        L->tel_entry_floats = kTelHeaderFloats + off;
+        const size_t bytes = (size_t)L->tel_depth * L->tel_entry_floats * 4;
+        void* h = nullptr;
+        if (cudaHostAlloc(&h, bytes, cudaHostAllocMapped) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(L, RTC_ENOMEM, "page-locked telemetry buffer of " + std::to_string(bytes) + " bytes");
+        }
+        L->h_tel = static_cast<float*>(h);
+        std::memset(h, 0xff, bytes);          // no entry valid yet (index all ones)
+        void* d = nullptr;
+        CK(L, cudaHostGetDevicePointer(&d, h, 0));
+        L->d_tel = static_cast<float*>(d);
+        TRY(dev_alloc(L, &L->d_telctr, 3 * sizeof(unsigned long long)));
+        CK(L, cudaMemset(L->d_telctr, 0, 3 * sizeof(unsigned long long)));
     }
     TRY(dev_alloc(L, &L->d_tiles_done, sizeof(unsigned)));
     CK(L, cudaMemset(L->d_tiles_done, 0, sizeof(unsigned)));
@@ -786,6 +841,16 @@ int apply_pending_update(rtc_loop* L) {
     return RTC_OK;
 }
 
+// Wait until the GPU no longer uses what the slot's previous frame left there:
+// its commands (and the input frames of graph mode) once its POLC product has
+// run; with a telemetry buffer, also its frame id, until its entry is written.
+int slot_wait(rtc_loop* L, const Slot& prev, int slot) {
+    if (!prev.seq) return RTC_OK;
+    if (L->h_done[slot] != prev.seq) CK(L, cudaEventSynchronize(prev.ev_polc));
+    if (L->tel_depth) CK(L, cudaEventSynchronize(prev.ev_tel));
+    return RTC_OK;
+}
+
 // Start a frame: pick its ring slot (discarding an unread frame that still holds it,
 // and waiting for the GPU to finish a frame that still uses it).
 int begin_frame(rtc_loop* L, uint64_t id, bool chunked) {
@@ -794,7 +859,7 @@ int begin_frame(rtc_loop* L, uint64_t id, bool chunked) {
     L->cur_slot = (int)(L->seq % (uint64_t)L->ring);
     {
         Slot& prev = L->slots[L->cur_slot];
-        if (prev.seq && L->h_done[L->cur_slot] != prev.seq) CK(L, cudaEventSynchronize(prev.ev_polc));
+        TRY(slot_wait(L, prev, L->cur_slot));
     }
     {
         std::lock_guard<std::mutex> g(L->mu);
@@ -809,6 +874,7 @@ int begin_frame(rtc_loop* L, uint64_t id, bool chunked) {
         s.chunked = chunked;
         s.seq = ++L->frame_seq;
         L->h_seq[L->cur_slot] = s.seq;
+        L->h_fid[L->cur_slot] = id;
     }
     std::fill(L->rows_in.begin(), L->rows_in.end(), 0);
     std::fill(L->rows_done.begin(), L->rows_done.end(), 0);
@@ -824,6 +890,34 @@ int record(rtc_loop* L, cudaEvent_t e, cudaStream_t st) {
     return RTC_OK;
 }
 
+TelArgs tel_args(rtc_loop* L) {
+    TelArgs t{};
+    t.blocks = L->d_blocks;
+    t.nblk = L->nblk;
+    t.na = L->na;
+    t.ns = L->ns;
+    t.nwfs = L->nwfs;
+    for (int k = 0; k < L->nwfs; ++k) t.blk_start[k] = L->wfs_blk0[k];
+    t.blk_start[L->nwfs] = L->nblk;
+    t.s_pad = L->d_s;
+    t.a = L->d_a;
+    t.part = L->d_part;
+    t.scale = L->d_Mscale;
+    t.streams = L->tel_streams;
+    t.off_s = L->tel_off_s;
+    t.off_a = L->tel_off_a;
+    t.off_p = L->tel_off_p;
+    t.decimate = L->tel_decimate;
+    t.depth = L->tel_depth;
+    t.entry_floats = L->tel_entry_floats;
+    t.ring = L->d_tel;
+    t.wcount = L->d_wcount;
+    t.ctr = L->d_telctr;
+    t.fid = L->d_fid + L->cur_slot;
+    t.t_cmd = L->d_tdone + L->cur_slot;
+    return t;
+}
+
 // After the MVM (whose tail wrote the commands): POLC for the next frame and the
 // telemetry copy.  Stream work only, so it can also be captured into a graph.
 int enqueue_tail(rtc_loop* L) {
@@ -832,10 +926,12 @@ int enqueue_tail(rtc_loop* L) {
     if (L->timing) TRY(record(L, s.ev_final, L->st));
     TRY(polc_product(L, !L->timing));
     TRY(record(L, s.ev_polc, L->st));
-    if (L->telemetry) {
+    if (L->telemetry || L->tel_depth) {
         CK(L, cudaStreamWaitEvent(L->st_tel, s.ev_polc, 0));
-        CK(L, launch_pack_slopes(L->d_blocks, L->nblk, std::max(L->max_cols, 1), L->d_s,
-                                 cmd + round_up((size_t)L->na, 4), L->st_tel));
+        if (L->telemetry)
+            CK(L, launch_pack_slopes(L->d_blocks, L->nblk, std::max(L->max_cols, 1), L->d_s,
+                                     cmd + round_up((size_t)L->na, 4), L->st_tel));
+        if (L->tel_depth) CK(L, launch_telemetry(tel_args(L), L->st_tel));
         TRY(record(L, s.ev_tel, L->st_tel));
         CK(L, cudaStreamWaitEvent(L->st, s.ev_tel, 0));   // the next frame rewrites the slopes
     } else {
@@ -893,6 +989,7 @@ FinaliseArgs fin_args(rtc_loop* L) {
     f.tiles_done = L->d_tiles_done;
     f.done_flag = L->d_done + L->cur_slot;
     f.seq = L->d_seq + L->cur_slot;
+    f.t_done = L->d_tdone + L->cur_slot;
     return f;
 }
 
@@ -1099,7 +1196,7 @@ int capture_graphs(rtc_loop* L) {
 int next_slot_free(rtc_loop* L, int* slot) {
     *slot = (int)(L->seq % (uint64_t)L->ring);
     const Slot& prev = L->slots[*slot];
-    if (prev.seq && L->h_done[*slot] != prev.seq) CK(L, cudaEventSynchronize(prev.ev_polc));
+    TRY(slot_wait(L, prev, *slot));
     return RTC_OK;
 }
 
@@ -1339,6 +1436,57 @@ int rtc_get_telemetry(rtc_loop* L, uint64_t frame_id, float* slopes, size_t ns, 
     if (cmds) std::memcpy(cmds, base, (size_t)L->na * 4);
     if (slopes) std::memcpy(slopes, base + round_up((size_t)L->na, 4), (size_t)L->ns * 4);
     return RTC_OK;
+}
+
+int rtc_telemetry_read(rtc_loop* L, rtc_tel_record* rec, float* slopes, size_t ns, float* cmds, size_t na,
+                       float* partials, size_t npartials, int64_t timeout_us) {
+    if (!L || !rec) return fail(L, RTC_EINVAL, "loop and rec are required");
+    if (!L->tel_depth) return fail(L, RTC_EINVAL, "loop has no telemetry buffer (tel_depth 0)");
+    if (slopes && (!(L->tel_streams & RTC_TEL_SLOPES) || ns != (size_t)L->ns))
+        return fail(L, RTC_EINVAL, "slopes not recorded, or ns wrong");
+    if (cmds && (!(L->tel_streams & RTC_TEL_COMMANDS) || na != (size_t)L->na))
+        return fail(L, RTC_EINVAL, "commands not recorded, or na wrong");
+    if (partials && (!(L->tel_streams & RTC_TEL_PARTIALS) || npartials != (size_t)L->nwfs * L->na))
+        return fail(L, RTC_EINVAL, "partial commands not recorded, or size not nwfs x na");
+    std::lock_guard<std::mutex> g(L->tel_mu);
+    const auto deadline = Clock::now() + std::chrono::microseconds(timeout_us < 0 ? 0 : timeout_us);
+    const uint64_t D = (uint64_t)L->tel_depth;
+    for (;;) {
+        const uint64_t w = __atomic_load_n(L->h_wcount, __ATOMIC_ACQUIRE);
+        if (L->tel_next >= w) {
+            if (timeout_us >= 0 && Clock::now() >= deadline) return fail(L, RTC_ETIMEDOUT, "no new telemetry entry");
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+            continue;
+        }
+        // the writer of entry w may be active, rewriting entry w - D: entries from w - D + 1 on are intact
+        if (w - L->tel_next > D - 1) {
+            L->tel_lost += w - (D - 1) - L->tel_next;
+            L->tel_next = w - (D - 1);
+        }
+        const float* e = L->h_tel + (size_t)(L->tel_next % D) * L->tel_entry_floats;
+        const TelHeader* h = reinterpret_cast<const TelHeader*>(e);
+        rtc_tel_record r{};
+        r.index = __atomic_load_n(&h->index, __ATOMIC_ACQUIRE);
+        r.frame_id = h->frame_id;
+        r.t_commands_ns = h->t_commands;
+        r.t_written_ns = h->t_written;
+        const float* body = e + kTelHeaderFloats;
+        if (slopes) std::memcpy(slopes, body + L->tel_off_s, (size_t)L->ns * 4);
+        if (cmds) std::memcpy(cmds, body + L->tel_off_a, (size_t)L->na * 4);
+        if (partials) std::memcpy(partials, body + L->tel_off_p, (size_t)L->nwfs * L->na * 4);
+        std::atomic_thread_fence(std::memory_order_acquire);
+        const uint64_t w2 = __atomic_load_n(L->h_wcount, __ATOMIC_ACQUIRE);
+        if (r.index != L->tel_next || w2 - L->tel_next > D - 1) {   // rewritten while it was copied
+            ++L->tel_lost;
+            ++L->tel_next;
+            continue;
+        }
+        r.lost = L->tel_lost;
+        L->tel_lost = 0;
+        ++L->tel_next;
+        *rec = r;
+        return RTC_OK;
+    }
 }
 
 int rtc_get_timing(rtc_loop* L, uint64_t frame_id, rtc_timing* out, int64_t timeout_us) {

@@ -37,7 +37,7 @@ def test_create_rejects_null_and_bad_geometry_without_gpu(rtc):
     w[0].kind, w[0].width, w[0].height = rtc.RTC_WFS_SH, 16, 16
     w[0].nsubx = w[0].nsuby = 3
     w[0].npx, w[0].nblocks = 8, 1          # 3 x 8 = 24 > 16: grid outside the frame
-    geo = rtc.rtc_geometry(1, w, 0, 0, 4)
+    geo = rtc.rtc_geometry(1, w, 0, 0, 4, 0, 0, 1)
     cm = rtc.rtc_cmat(1, 18, rtc.RTC_F32, C.c_void_p(1), None)
     pol = rtc.rtc_polc(None, 0, None, 0.5, 0.01, None, 0, 0.0, 0.0, 0, None, 0, None)
     assert rtc.lib.rtc_create(C.byref(geo), None, C.byref(cm), C.byref(pol), C.byref(h)) == rtc.RTC_EINVAL
@@ -86,7 +86,7 @@ def test_structs_mirror_the_header_layout(rtc, tmp_path):
     if shutil.which("gcc") is None:
         pytest.skip("gcc not available")
     structs = [rtc.rtc_wfs, rtc.rtc_geometry, rtc.rtc_calib, rtc.rtc_cmat, rtc.rtc_polc, rtc.rtc_chunk,
-               rtc.rtc_timing, rtc.rtc_update_desc, rtc.rtc_server_loop_info, rtc.rtc_info]
+               rtc.rtc_timing, rtc.rtc_tel_record, rtc.rtc_update_desc, rtc.rtc_server_loop_info, rtc.rtc_info]
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "rtc.h"', "int main(void) {"]
     for st in structs:
         n = st.__name__

@@ -182,3 +182,106 @@ def test_explicit_polc_loop_in_the_server_mix(rtc, torch_cuda):
             for j in range(2):
                 a = lps[j].get_commands(timeout_us=WAIT_US)[1]
                 assert rel(a, refs[j].step(frames[j][k])[1]) <= TOL_F32, (j, k)
+
+
+# ------------------------------------------------------------------ telemetry circular buffer
+
+ALL_TEL = 1 | 2 | 4      # RTC_TEL_SLOPES | RTC_TEL_COMMANDS | RTC_TEL_PARTIALS
+
+
+def oracle_partials(cfg, s):
+    """Per-WFS partial commands M~[:, cols_w] s[cols_w] in float64."""
+    from oracle import rtc_oracle as orc
+    m = orc.stored_matrix(cfg["M"], cfg.get("M_dtype", "f32"), cfg.get("M_scale"))
+    out, c0 = [], 0
+    for w in cfg["wfs"]:
+        n = 2 * synth.num_valid(w)
+        out.append(m[:, c0:c0 + n] @ s[c0:c0 + n])
+        c0 += n
+    return np.array(out)
+
+
+def test_telemetry_buffer_entries_match_the_oracle(rtc, torch_cuda):
+    cfg = ragged_global_config(seed=91)
+    frames = synth.draw_frames(cfg, 6, seed=92)
+    ref = OracleLoop(cfg)
+    with rtc.Loop(cfg, tel_depth=16, tel_streams=ALL_TEL) as loop:
+        for k, f in enumerate(frames):
+            loop.submit_frame(k + 1, f, [synth.chunk_plan(w, 3) for w in cfg["wfs"]])
+            loop.get_commands(timeout_us=WAIT_US)
+        t_prev = 0
+        for k, f in enumerate(frames):
+            rec, s, a, p = loop.telemetry_read(timeout_us=WAIT_US, partials=True)
+            s_ref, a_ref = ref.step(f)
+            assert rec["index"] == k and rec["frame_id"] == k + 1 and rec["lost"] == 0
+            assert rec["t_commands_ns"] > t_prev and rec["t_written_ns"] >= rec["t_commands_ns"]
+            t_prev = rec["t_commands_ns"]
+            assert rel(s, s_ref) <= TOL_F32 and rel(a, a_ref) <= TOL_F32
+            p_ref = oracle_partials(cfg, s_ref)
+            assert rel(p, p_ref) <= TOL_F32
+            assert rel(p.sum(axis=0), p_ref.sum(axis=0)) <= TOL_F32
+        with pytest.raises(rtc.RtcError, match="ETIMEDOUT"):
+            loop.telemetry_read(timeout_us=0)
+
+
+def test_telemetry_decimation_and_overrun_count_lost_entries(rtc, torch_cuda):
+    cfg = synth.make_config("scao_small")
+    frames = synth.draw_frames(cfg, 2, seed=93)
+    with rtc.Loop(cfg, tel_depth=4, tel_streams=2, tel_decimate=3) as loop:
+        cmds = {}
+        for k in range(20):
+            loop.submit_frame(k + 1, frames[k % 2])
+            cmds[k + 1] = loop.get_commands(timeout_us=WAIT_US)[1]
+        loop.sync()
+        # frames 1, 4, ..., 19 were recorded as entries 0..6; a reader that fell behind a
+        # depth-4 buffer gets the newest three and counts the four before them lost
+        got = []
+        for _ in range(3):
+            rec, s, a, _ = loop.telemetry_read(timeout_us=WAIT_US, slopes=False)
+            assert s is None and np.array_equal(a, cmds[rec["frame_id"]])
+            got.append((rec["index"], rec["frame_id"], rec["lost"]))
+        assert got == [(4, 13, 4), (5, 16, 0), (6, 19, 0)]
+        with pytest.raises(rtc.RtcError, match="EINVAL"):
+            loop.telemetry_read(timeout_us=0, slopes=True)          # slopes were not recorded
+
+
+def test_telemetry_reader_thread_while_frames_run(rtc, torch_cuda):
+    import threading
+    cfg = synth.make_config("elt_scao_sh", polc=True)
+    frames = synth.draw_frames(cfg, 2, seed=94)
+    n = 150
+    with rtc.Loop(cfg, tel_depth=32, tel_streams=ALL_TEL, graphs=True, ring=3) as loop:
+        seen, lost = [], [0]
+
+        def reader():
+            while len(seen) + lost[0] < n:
+                try:
+                    rec, s, a, p = loop.telemetry_read(timeout_us=2_000_000, partials=True)
+                except rtc.RtcError:
+                    return
+                lost[0] += rec["lost"]
+                seen.append((rec["index"], rec["frame_id"], a))
+
+        th = threading.Thread(target=reader)
+        th.start()
+        cmds = {}
+        for k in range(n):
+            for b, x in zip(loop.next_frame_buffers(), frames[k % 2]):
+                b[:] = x
+            loop.submit_graph(k + 1)
+            fid, a = loop.get_commands(timeout_us=WAIT_US)
+            cmds[fid] = a
+        th.join(timeout=60)
+        assert not th.is_alive()
+    assert len(seen) + lost[0] == n and len(seen) > 0
+    idx = [i for i, _, _ in seen]
+    assert idx == sorted(idx) and len(set(idx)) == len(idx)
+    for i, fid, a in seen:
+        assert fid == i + 1 and np.array_equal(a, cmds[fid])
+
+
+def test_loop_without_telemetry_buffer_rejects_reads(rtc, torch_cuda):
+    cfg = synth.make_config("scao_small")
+    with rtc.Loop(cfg) as loop:
+        with pytest.raises(rtc.RtcError, match="no telemetry buffer"):
+            loop.telemetry_read(timeout_us=0)
