@@ -725,6 +725,114 @@ def serving_arm(args):
     print(json.dumps(out), flush=True)
 
 
+def variants_arm(args):
+    """The hot path's variants, each against its baseline on the same loop:
+    (1) implicit POLC (P, na x na, after the command) against explicit POLC (u = D a, ns x na, after the
+        command; s + u formed in the slope kernel), MCAO FP32 (Section 3.4);
+    (2) camera-paced MCAO FP32 latency while every frame's slopes, commands and per-WFS partial commands
+        are recorded in the telemetry circular buffer and a library thread streams them to a file
+        descriptor (Section 3.3), against the same loop without telemetry;
+    (3) local against global normalisation of the ELT pyramid, FP32 and BF16."""
+    import torch
+    from paper_1903_01852_gb300 import binding as rtc
+    from paper_1903_01852_gb300 import synth
+    torch.cuda.set_device(0)
+    sampler = ClockSampler(0)
+    sampler.start()
+    n_paced, n_warm = args.variant_frames, 300
+
+    def dev_copy(frames):
+        out = []
+        for f in frames:
+            per = []
+            for x in f:
+                h, w = x.shape
+                t = torch.zeros((h, (w + 7) // 8 * 8), dtype=torch.int16, device="cuda")
+                t[:, :w] = torch.from_numpy(x.view(np.int16)).cuda()
+                per.append(t[:, :w])
+            out.append(per)
+        return out
+
+    def pinned_copy(frames):
+        out = []
+        for f in frames:
+            per = []
+            for x in f:
+                t = torch.empty(x.shape, dtype=torch.int16, pin_memory=True)
+                t.numpy()[:] = x.view(np.int16)
+                per.append(t)
+            out.append(per)
+        return out
+
+    out = {"mode": "variants", "unit": "us"}
+    try:
+        cfg, frames = make_workload()
+        dev, host = dev_copy(frames), pinned_copy(frames)
+        plans = [synth.chunk_plan(w, NCHUNKS if w["nsubx"] > 2 else 1) for w in cfg["wfs"]]
+        # (1) POLC forms
+        rng = np.random.default_rng(7)
+        exp_cfg = dict(cfg, P=None, polc="explicit", D=synth.interaction_matrix(rng, cfg["ns"], cfg["na"]))
+        polc = {}
+        for name, c in (("implicit", cfg), ("explicit", exp_cfg)):
+            with rtc.Loop(c, stage_timing=True) as sl:
+                rows, _ = run_unpaced_timed(sl, dev, 200, 20, sampler, 1)
+                pbytes = sl.info()["p_bytes"]
+            with rtc.Loop(c, timing=True) as lp:
+                ms, _, _, fid = run_unpaced(lp, dev, 300, 20, torch, sampler, 1)
+                lat, _ = run_host_path(lp, host, plans, n_paced, n_warm, sampler, fid, paced=True)
+            polc_us = statistics.median([r["polc_us"] for r in rows])
+            polc[name] = {"polc_product_us": polc_us, "polc_matrix_bytes": pbytes,
+                          "polc_gbs": pbytes / (polc_us * 1e-6) / 1e9,
+                          "unpaced_frame_period_us": ms * 1000.0 / 300, "paced_latency_us": stats(lat)}
+        del exp_cfg
+        out["polc"] = {"definition": "polc_product_us: the POLC kernel after the command (stage timing, "
+                                     "serialised); unpaced_frame_period_us: back-to-back frames from HBM; "
+                                     "paced_latency_us: last pixel in -> commands returned at "
+                                     f"{PACED_HZ:.0f} Hz", **polc}
+        # (2) telemetry streaming
+        tel = {}
+        all_streams = rtc.RTC_TEL_SLOPES | rtc.RTC_TEL_COMMANDS | rtc.RTC_TEL_PARTIALS
+        with rtc.Loop(cfg, timing=True) as lp:
+            lat, _ = run_host_path(lp, host, plans, n_paced, n_warm, sampler, 1, paced=True)
+            tel["without"] = stats(lat)
+        with rtc.Loop(cfg, timing=True, tel_depth=1000, tel_streams=all_streams) as lp, \
+                open(os.devnull, "wb") as sink:
+            lp.telemetry_stream_start(sink.fileno())
+            lat, _ = run_host_path(lp, host, plans, n_paced, n_warm, sampler, 1, paced=True)
+            lp.sync()
+            st = lp.telemetry_stream_stop()
+            tel["with"] = stats(lat)
+            tel["stream"] = st
+            tel["entry_bytes"] = st["bytes"] // max(st["entries"], 1)
+        out["telemetry"] = {"definition": "paced MCAO FP32, last pixel in -> commands returned; 'with': every "
+                                          "frame's slopes, commands and 9 per-WFS partial command vectors written "
+                                          "by the GPU into a 1000-entry page-locked circular buffer, drained by the "
+                                          "library's stream thread (copy out of the buffer, write() to /dev/null)",
+                            **tel}
+        del cfg, frames, dev, host
+        torch.cuda.empty_cache()
+        # (3) pyramid normalisation
+        pcfg = synth.make_config("elt_scao_pyramid")
+        pframes = synth.draw_frames(pcfg, FRAME_RING, seed=3)
+        pdev = dev_copy(pframes)
+        pyr = {}
+        for norm in ("local", "global"):
+            c = dict(pcfg, wfs=[dict(pcfg["wfs"][0], norm=norm)])
+            for fmt, cc in (("f32", c), ("bf16", bf16_config(c, rtc, torch))):
+                with rtc.Loop(cc, stage_timing=True) as sl:
+                    rows, _ = run_unpaced_timed(sl, pdev, 500, 50, sampler, 1)
+                with rtc.Loop(cc, timing=True) as lp:
+                    rl, _ = run_unpaced_timed(lp, pdev, 1000, 50, sampler, 1)
+                pyr[f"{norm}_{fmt}"] = {"slopes_us": statistics.median([r["slopes_us"] for r in rows]),
+                                        "latency_us": stats([r["latency_us"] for r in rl])}
+        out["pyramid_norm"] = {"definition": "ELT SCAO pyramid, frames from HBM, unpaced: slope-kernel time "
+                                             "(stage timing) and frame latency (device events)", **pyr}
+    finally:
+        sampler.stop()
+    out["clocks"] = sampler.summary()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -738,6 +846,9 @@ def main():
     ap.add_argument("--swap-frames", type=int, default=2500, help="paced frames of the parameter-swap run")
     ap.add_argument("--serving", action="store_true", help="serving mix (LTAO + MCAO + 2 SCAO) instead")
     ap.add_argument("--serving-seconds", type=float, default=4.0)
+    ap.add_argument("--variants", action="store_true",
+                    help="POLC forms, telemetry streaming, pyramid normalisation instead")
+    ap.add_argument("--variant-frames", type=int, default=3000, help="paced frames per --variants case")
     ap.add_argument("--workload", default="mcao", help="configuration (profiling aid; the bench line is mcao)")
     ap.add_argument("--quick", action="store_true", help="profiling aid: only the unpaced loop")
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "e4m3"], help="matrix storage for --quick")
@@ -751,6 +862,9 @@ def main():
     elif args.serving:
         if rank == 0:
             serving_arm(args)
+    elif args.variants:
+        if rank == 0:
+            variants_arm(args)
     else:
         ours_arm(args, world, rank, local)
     if world > 1:

@@ -321,6 +321,28 @@ typedef struct rtc_tel_record {
 int rtc_telemetry_read(rtc_loop* loop, rtc_tel_record* rec, float* slopes, size_t ns, float* cmds, size_t na,
                        float* partials, size_t npartials, int64_t timeout_us);
 
+/* Telemetry streaming (Section 3.3: DARC reads its circular buffers and sends
+ * the telemetry on, e.g. to disk): a library thread takes over as the
+ * buffer's reader and writes every entry it gets to the file descriptor fd,
+ * as the rtc_tel_record (40 bytes) followed by the recorded sections in the
+ * order slopes, commands, partial commands (float32).  fd stays owned by the
+ * caller and must stay open until rtc_telemetry_stream_stop.  While a stream
+ * runs, rtc_telemetry_read returns RTC_EINVAL.  RTC_EINVAL without a
+ * telemetry buffer or when a stream already runs. */
+int rtc_telemetry_stream_start(rtc_loop* loop, int fd);
+
+typedef struct rtc_tel_stream_stats {
+    uint64_t entries;            /* entries written to fd */
+    uint64_t lost;               /* entries the stream lost (overwritten before it read them) */
+    uint64_t bytes;              /* bytes written */
+    int32_t write_error;         /* errno of the first failed write (the stream then stops), or 0 */
+} rtc_tel_stream_stats;
+
+/* Stop the stream: the thread first writes every entry already published,
+ * then exits; *stats (may be NULL) receives its totals.  RTC_EINVAL when no
+ * stream runs. */
+int rtc_telemetry_stream_stop(rtc_loop* loop, rtc_tel_stream_stats* stats);
+
 /* ---- parameter double buffer (Section 3.2) ----------------------------- */
 
 /* New parameters for a running loop.  Every pointer may be NULL (unchanged);

@@ -81,6 +81,10 @@ class rtc_tel_record(C.Structure):
                 ("t_written_ns", C.c_uint64), ("lost", C.c_uint64)]
 
 
+class rtc_tel_stream_stats(C.Structure):
+    _fields_ = [("entries", C.c_uint64), ("lost", C.c_uint64), ("bytes", C.c_uint64), ("write_error", C.c_int32)]
+
+
 class rtc_update_desc(C.Structure):
     _fields_ = [("M", C.c_void_p), ("M_scale", f32p), ("P", C.c_void_p), ("P_scale", f32p),
                 ("dark", C.POINTER(f32p)), ("flat", C.POINTER(f32p)), ("threshold", f32p), ("ref_slopes", f32p),
@@ -116,6 +120,8 @@ SIGNATURES = [
     ("rtc_get_timing", C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(rtc_timing), C.c_int64]),
     ("rtc_telemetry_read", C.c_int, [C.c_void_p, C.POINTER(rtc_tel_record), f32p, C.c_size_t, f32p, C.c_size_t,
                                      f32p, C.c_size_t, C.c_int64]),
+    ("rtc_telemetry_stream_start", C.c_int, [C.c_void_p, C.c_int]),
+    ("rtc_telemetry_stream_stop", C.c_int, [C.c_void_p, C.POINTER(rtc_tel_stream_stats)]),
     ("rtc_update", C.c_int, [C.c_void_p, C.POINTER(rtc_update_desc)]),
     ("rtc_get_state", C.c_int, [C.c_void_p, f32p, C.c_size_t]),
     ("rtc_set_state", C.c_int, [C.c_void_p, f32p, C.c_size_t]),
@@ -384,6 +390,15 @@ class Loop:
                                       self.na if cmds else 0, ptr(p), nw * self.na if partials else 0,
                                       int(timeout_us)), self._h)
         return {k: getattr(r, k) for k, _ in rtc_tel_record._fields_}, s, a, p
+
+    def telemetry_stream_start(self, fd):
+        """rtc_telemetry_stream_start: a library thread writes every entry to the file descriptor fd."""
+        _check(lib.rtc_telemetry_stream_start(self._h, int(fd)), self._h)
+
+    def telemetry_stream_stop(self):
+        st = rtc_tel_stream_stats()
+        _check(lib.rtc_telemetry_stream_stop(self._h, C.byref(st)), self._h)
+        return {k: getattr(st, k) for k, _ in rtc_tel_stream_stats._fields_}
 
     def get_timing(self, frame_id, timeout_us=-1):
         t = rtc_timing()

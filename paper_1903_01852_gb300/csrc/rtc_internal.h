@@ -27,10 +27,9 @@ struct WfsDev {
     int calib_pitch;          // floats per calibration-map row (multiple of 4)
     int sh_groups;            // SH: row groups per CTA in the column-sum phase
     // pyramid with global normalisation (norm == RTC_NORM_GLOBAL): its slope rows
-    // are always launched together; the last of them to finish normalises all
+    // are always launched together, then normalised by a second kernel
     int norm;
-    int grow0, gnrows;        // its slope rows in the row table
-    int gblk0, gnblk;         // its column blocks
+    int gnrows;               // its slope rows
     int gpix;                 // valid pupil pixels
     int gflux;                // float offset of the per-row flux sums in the part scratch
 };
@@ -130,11 +129,17 @@ struct TelArgs {
 };
 cudaError_t launch_telemetry(const TelArgs& t, cudaStream_t st);
 
+// Global pyramid normalisation over items [item0, item0 + nitems) (each a column
+// block and its WFS); max_pairs bounds the slope pairs of one block.  pdl: a
+// programmatic dependent of the slope kernel before it in the stream.
+cudaError_t launch_normalise(const int2* items, int item0, int nitems, int max_pairs, const BlockDev* blocks,
+                             const WfsDev* wfs, const float* pscr, const float* ref, const float* pol, float* s_pad,
+                             bool pdl, cudaStream_t st);
+
 // Slope kernel over the part table entries [part0, part0 + nparts).  Each slope
-// is (measured - ref) + pol, with ref and pol (compact slope order) optional;
-// blocks (the column-block table) locates a globally normalised WFS's slopes.
+// is (measured - ref) + pol, with ref and pol (compact slope order) optional.
 cudaError_t launch_slopes(const SlopePart* parts, int part0, int nparts, const SlopeRow* rows,
-                          const WfsDev* wfs, const BlockDev* blocks, const FramePtrs& fp, const uint16_t* xlist,
+                          const WfsDev* wfs, const FramePtrs& fp, const uint16_t* xlist,
                           const float* ref, const float* pol, float* s_pad, float* pscr, unsigned* counters,
                           int smem_bytes, cudaStream_t st);
 

@@ -212,13 +212,11 @@ __device__ void sh_part(const SlopePart& P, const SlopeRow& row, const WfsDev& W
 // of the four pupil images A (top-left), B (top-right), C (bottom-left),
 // D (bottom-right); sx = (A+C-B-D)/N, sy = (A+B-C-D)/N with N = A+B+C+D.
 // With global normalisation the row stores the differences themselves and its
-// flux sum; the last row of the WFS to finish (they are launched together)
-// divides every difference by the mean flux over the valid pupil pixels.
-__device__ void pyr_row(const SlopeRow& row, const WfsDev& W, const BlockDev* __restrict__ blocks,
-                        const uint16_t* __restrict__ px, long long pitch, int prow0,
-                        const uint16_t* __restrict__ xlist, const float* __restrict__ ref,
-                        const float* __restrict__ pol, float* __restrict__ s_pad, float* __restrict__ pscr,
-                        unsigned* __restrict__ counters) {
+// flux sum (per-thread sums in unit order, then a fixed reduction over the CTA);
+// normalise_kernel divides them by the mean flux once every row is done.
+__device__ void pyr_row(const SlopeRow& row, const WfsDev& W, const uint16_t* __restrict__ px, long long pitch,
+                        int prow0, const uint16_t* __restrict__ xlist, const float* __restrict__ ref,
+                        const float* __restrict__ pol, float* __restrict__ s_pad, float* __restrict__ pscr) {
     const int i = row.row;
     const bool global = W.norm == RTC_NORM_GLOBAL;
     float flux = 0.f;
@@ -246,11 +244,7 @@ __device__ void pyr_row(const SlopeRow& row, const WfsDev& W, const BlockDev* __
         store_pair(s_pad, row.s_pad + 2 * u, ref, pol, row.s_compact + 2 * u, sx, sy);
     }
     if (!global) return;
-
-    // row flux: per-thread sums in unit order, then a fixed reduction over the CTA
     __shared__ float s_red[kSlopeThreads / 32];
-    __shared__ int s_last;
-    __shared__ float s_mean;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     flux = warp_sum(flux);
     if (lane == 0) s_red[warp] = flux;
@@ -260,44 +254,6 @@ __device__ void pyr_row(const SlopeRow& row, const WfsDev& W, const BlockDev* __
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) f += s_red[w];
         pscr[W.gflux + i] = f;
     }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&counters[W.grow0], 1u) == (unsigned)(W.gnrows - 1);
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    if (warp == 0) {
-        float f = 0.f;
-        for (int r = lane; r < W.gnrows; r += 32) f += __ldcg(pscr + W.gflux + r);
-        f = warp_sum(f);
-        if (lane == 0) s_mean = f / float(W.gpix);
-    }
-    __syncthreads();
-    const float mean = s_mean;
-    // every slope pair of the WFS, block by block; eight pairs of loads in flight per thread
-    constexpr int kU = 8;
-    for (int b = W.gblk0; b < W.gblk0 + W.gnblk; ++b) {
-        const BlockDev B = blocks[b];
-        const int npair = B.ncols >> 1;
-        for (int q0 = threadIdx.x; q0 < npair; q0 += kU * blockDim.x) {
-            float2 d[kU];
-#pragma unroll
-            for (int k = 0; k < kU; ++k) {
-                const int q = q0 + k * blockDim.x;
-                d[k] = q < npair ? __ldcg(reinterpret_cast<const float2*>(s_pad + B.x_off) + q) : make_float2(0.f, 0.f);
-            }
-#pragma unroll
-            for (int k = 0; k < kU; ++k) {
-                const int q = q0 + k * blockDim.x;
-                if (q < npair) {
-                    float sx = 0.f, sy = 0.f;
-                    if (mean > 0.f) { sx = d[k].x / mean; sy = d[k].y / mean; }
-                    store_pair(s_pad, B.x_off + 2 * q, ref, pol, B.c0 + 2 * q, sx, sy);
-                }
-            }
-        }
-    }
-    if (threadIdx.x == 0) counters[W.grow0] = 0u;
 }
 
 struct SlopeArgs {
@@ -305,7 +261,6 @@ struct SlopeArgs {
     int part0;
     const SlopeRow* rows;
     const WfsDev* wfs;
-    const BlockDev* blocks;
     FramePtrs fp;
     const uint16_t* xlist;
     const float* ref;
@@ -325,8 +280,64 @@ __global__ void __launch_bounds__(kSlopeThreads) slopes_kernel(const __grid_cons
         sh_part(P, row, W, a.fp.px[row.wfs], a.fp.pitch[row.wfs], a.fp.row0[row.wfs], a.xlist, a.ref, a.pol, a.s_pad,
                 a.pscr, a.counters, sm);
     else
-        pyr_row(row, W, a.blocks, a.fp.px[row.wfs], a.fp.pitch[row.wfs], a.fp.row0[row.wfs], a.xlist, a.ref, a.pol,
-                a.s_pad, a.pscr, a.counters);
+        pyr_row(row, W, a.fp.px[row.wfs], a.fp.pitch[row.wfs], a.fp.row0[row.wfs], a.xlist, a.ref, a.pol, a.s_pad,
+                a.pscr);
+}
+
+// Global normalisation of pyramid slopes, a programmatic dependent of the slope
+// kernel: grid.y enumerates column blocks of globally normalised WFS (items:
+// block, WFS), grid.x their slope pairs.  Every CTA adds the WFS's row fluxes
+// in the same fixed order (so all agree on the mean bit for bit), then divides
+// its pairs by the mean flux over the valid pupil pixels.
+struct NormArgs {
+    const int2* items;
+    int item0;
+    const BlockDev* blocks;
+    const WfsDev* wfs;
+    const float* pscr;
+    const float* ref;
+    const float* pol;
+    float* s_pad;
+};
+
+__global__ void __launch_bounds__(256) normalise_kernel(const __grid_constant__ NormArgs a) {
+    __shared__ float s_mean;
+    pdl_trigger();        // the MVM may launch and prefetch now
+    pdl_wait();           // differences and row fluxes are written by the slope kernel
+    const int2 it = a.items[a.item0 + blockIdx.y];
+    const WfsDev& W = a.wfs[it.y];
+    if (threadIdx.x < 32) {
+        float f = 0.f;
+        for (int r = threadIdx.x; r < W.gnrows; r += 32) f += a.pscr[W.gflux + r];
+        f = warp_sum(f);
+        if (threadIdx.x == 0) s_mean = f / float(W.gpix);
+    }
+    __syncthreads();
+    const BlockDev B = a.blocks[it.x];
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (B.ncols >> 1)) return;
+    const float mean = s_mean;
+    const float2 d = reinterpret_cast<const float2*>(a.s_pad + B.x_off)[q];
+    float sx = 0.f, sy = 0.f;
+    if (mean > 0.f) { sx = d.x / mean; sy = d.y / mean; }
+    store_pair(a.s_pad, B.x_off + 2 * q, a.ref, a.pol, B.c0 + 2 * q, sx, sy);
+}
+
+cudaError_t launch_normalise(const int2* items, int item0, int nitems, int max_pairs, const BlockDev* blocks,
+                             const WfsDev* wfs, const float* pscr, const float* ref, const float* pol, float* s_pad,
+                             bool pdl, cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    NormArgs a{items, item0, blocks, wfs, pscr, ref, pol, s_pad};
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)std::max(1, (max_pairs + 255) / 256), (unsigned)nitems);
+    cfg.blockDim = dim3(256);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, normalise_kernel, a);
 }
 
 cudaError_t configure_slopes(int smem_bytes) {
@@ -335,11 +346,10 @@ cudaError_t configure_slopes(int smem_bytes) {
 }
 
 cudaError_t launch_slopes(const SlopePart* parts, int part0, int nparts, const SlopeRow* rows, const WfsDev* wfs,
-                          const BlockDev* blocks, const FramePtrs& fp, const uint16_t* xlist, const float* ref,
-                          const float* pol, float* s_pad, float* pscr, unsigned* counters, int smem_bytes,
-                          cudaStream_t st) {
+                          const FramePtrs& fp, const uint16_t* xlist, const float* ref, const float* pol,
+                          float* s_pad, float* pscr, unsigned* counters, int smem_bytes, cudaStream_t st) {
     if (nparts <= 0) return cudaSuccess;
-    SlopeArgs a{parts, part0, rows, wfs, blocks, fp, xlist, ref, pol, s_pad, pscr, counters};
+    SlopeArgs a{parts, part0, rows, wfs, fp, xlist, ref, pol, s_pad, pscr, counters};
     slopes_kernel<<<nparts, kSlopeThreads, smem_bytes, st>>>(a);
     return cudaGetLastError();
 }

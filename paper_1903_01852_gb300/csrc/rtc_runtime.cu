@@ -13,6 +13,9 @@
 #include <thread>
 #include <vector>
 
+#include <cerrno>
+#include <unistd.h>
+
 #include "rtc_internal.h"
 
 using namespace rtc;
@@ -56,6 +59,10 @@ struct rtc_loop {
     std::vector<int> row_ready;     // per table row: pixel rows of its WFS needed
     std::vector<int> part_start;    // per table row (+1): first slope-kernel part of the row
     std::vector<int> blk_row_end;   // per block: end (exclusive) of its slope rows within the WFS
+    std::vector<int2> norm_items;   // column blocks of globally normalised pyramids (block, WFS)
+    std::vector<int> norm_item0, norm_nitems;   // per WFS: its range in norm_items
+    int norm_max_pairs = 0;
+    int2* d_norm_items = nullptr;
     std::vector<BlockDev> blocks_h;
     int max_cols = 0, smem_bytes = 0;
     uint64_t m_bytes = 0, p_bytes = 0, pixel_bytes = 0, device_bytes = 0;
@@ -168,6 +175,9 @@ struct rtc_loop {
     unsigned long long* d_telctr = nullptr;   // device counters of the telemetry kernel
     std::mutex tel_mu;                        // one reader at a time
     uint64_t tel_next = 0, tel_lost = 0;
+    std::thread tel_thread;                   // rtc_telemetry_stream_start's drain thread
+    std::atomic<bool> tel_streaming{false}, tel_stop{false};
+    rtc_tel_stream_stats tel_stats{};
 
     // graph mode (RTC_FLAG_GRAPHS): per ring slot, page-locked input frames and a captured frame graph
     bool graphs = false;
@@ -234,8 +244,17 @@ int dev_alloc(rtc_loop* L, T** p, size_t bytes) {
         if (r_ != RTC_OK) return r_; \
     } while (0)
 
+void stop_stream(rtc_loop* L) {
+    if (L->tel_thread.joinable()) {
+        L->tel_stop = true;
+        L->tel_thread.join();
+    }
+    L->tel_streaming = false;
+}
+
 void release(rtc_loop* L) {
     if (!L) return;
+    stop_stream(L);
     if (!L->cuda_touched) {
         delete L;
         return;
@@ -466,10 +485,7 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
             return fail(L, RTC_EINVAL, "bad threshold mode");
         D.calib_pitch = (int)round_up((size_t)w.width, 4);
         D.norm = sh ? RTC_NORM_LOCAL : w.norm;
-        D.grow0 = L->wfs_row0[k];
         D.gnrows = nr;
-        D.gblk0 = L->wfs_blk0[k];
-        D.gnblk = w.nblocks;
         D.gpix = 0;
         for (int i = 0; i < nr; ++i) D.gpix += (int)row_x[i].size();
         if (sh) {
@@ -517,11 +533,20 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
         }
     }
     L->part_start.push_back((int)parts.size());
-    for (int k = 0; k < L->nwfs; ++k)          // per-row flux sums of globally normalised pyramids
-        if (wdev[k].norm == RTC_NORM_GLOBAL) {
-            wdev[k].gflux = (int)pscr_floats;
-            pscr_floats += (size_t)wdev[k].gnrows;
+    // globally normalised pyramids: per-row flux sums, and their column blocks for the normalisation kernel
+    L->norm_item0.assign(L->nwfs, 0);
+    L->norm_nitems.assign(L->nwfs, 0);
+    for (int k = 0; k < L->nwfs; ++k) {
+        L->norm_item0[k] = (int)L->norm_items.size();
+        if (wdev[k].norm != RTC_NORM_GLOBAL) continue;
+        wdev[k].gflux = (int)pscr_floats;
+        pscr_floats += (size_t)wdev[k].gnrows;
+        for (int b = L->wfs_blk0[k]; b < L->wfs_blk0[k] + L->wfs_nblk[k]; ++b) {
+            L->norm_items.push_back(int2{b, k});
+            L->norm_max_pairs = std::max(L->norm_max_pairs, L->blocks_h[b].ncols / 2);
         }
+        L->norm_nitems[k] = L->wfs_nblk[k];
+    }
     L->nfin = (L->na + kFinRows - 1) / kFinRows;
     L->ns = compact;
     if (M->ns != L->ns)
@@ -703,6 +728,11 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
     CK(L, cudaMemset(L->d_row_cnt, 0, (size_t)L->nrows * sizeof(unsigned)));
     TRY(dev_alloc(L, &L->d_fin_cnt, (size_t)L->nfin * sizeof(unsigned)));
     CK(L, cudaMemset(L->d_fin_cnt, 0, (size_t)L->nfin * sizeof(unsigned)));
+    if (!L->norm_items.empty()) {
+        TRY(dev_alloc(L, &L->d_norm_items, L->norm_items.size() * sizeof(int2)));
+        CK(L, cudaMemcpy(L->d_norm_items, L->norm_items.data(), L->norm_items.size() * sizeof(int2),
+                         cudaMemcpyHostToDevice));
+    }
     TRY(dev_alloc(L, &L->d_xlist, std::max<size_t>(xlist.size(), 1) * 2));
     if (!xlist.empty()) CK(L, cudaMemcpy(L->d_xlist, xlist.data(), xlist.size() * 2, cudaMemcpyHostToDevice));
     if (C && C->ref_slopes) {
@@ -995,8 +1025,19 @@ FinaliseArgs fin_args(rtc_loop* L) {
 
 int slopes_rows(rtc_loop* L, int r0, int r1, const FramePtrs& fp, cudaStream_t st) {
     const int p0 = L->part_start[r0], p1 = L->part_start[r1];
-    CK(L, launch_slopes(L->d_parts, p0, p1 - p0, L->d_rows, L->d_wfs, L->d_blocks, fp, L->d_xlist, L->d_ref,
-                        L->explicit_polc ? L->d_u : nullptr, L->d_s, L->d_pscr, L->d_row_cnt, L->smem_bytes, st));
+    const float* pol = L->explicit_polc ? L->d_u : nullptr;
+    CK(L, launch_slopes(L->d_parts, p0, p1 - p0, L->d_rows, L->d_wfs, fp, L->d_xlist, L->d_ref, pol, L->d_s,
+                        L->d_pscr, L->d_row_cnt, L->smem_bytes, st));
+    // globally normalised pyramids whose rows all ran here (they are never split across launches)
+    int i0 = -1, i1 = -1;
+    for (int k = 0; k < L->nwfs; ++k)
+        if (L->norm_nitems[k] && L->wfs_row0[k] >= r0 && L->wfs_row0[k] + L->wfs_nrows[k] <= r1) {
+            if (i0 < 0) i0 = L->norm_item0[k];
+            i1 = L->norm_item0[k] + L->norm_nitems[k];
+        }
+    if (i0 >= 0)
+        CK(L, launch_normalise(L->d_norm_items, i0, i1 - i0, L->norm_max_pairs, L->d_blocks, L->d_wfs, L->d_pscr,
+                               L->d_ref, pol, L->d_s, !L->stage_timing, st));
     return RTC_OK;
 }
 
@@ -1438,23 +1479,16 @@ int rtc_get_telemetry(rtc_loop* L, uint64_t frame_id, float* slopes, size_t ns, 
     return RTC_OK;
 }
 
-int rtc_telemetry_read(rtc_loop* L, rtc_tel_record* rec, float* slopes, size_t ns, float* cmds, size_t na,
-                       float* partials, size_t npartials, int64_t timeout_us) {
-    if (!L || !rec) return fail(L, RTC_EINVAL, "loop and rec are required");
-    if (!L->tel_depth) return fail(L, RTC_EINVAL, "loop has no telemetry buffer (tel_depth 0)");
-    if (slopes && (!(L->tel_streams & RTC_TEL_SLOPES) || ns != (size_t)L->ns))
-        return fail(L, RTC_EINVAL, "slopes not recorded, or ns wrong");
-    if (cmds && (!(L->tel_streams & RTC_TEL_COMMANDS) || na != (size_t)L->na))
-        return fail(L, RTC_EINVAL, "commands not recorded, or na wrong");
-    if (partials && (!(L->tel_streams & RTC_TEL_PARTIALS) || npartials != (size_t)L->nwfs * L->na))
-        return fail(L, RTC_EINVAL, "partial commands not recorded, or size not nwfs x na");
-    std::lock_guard<std::mutex> g(L->tel_mu);
+// The oldest unread entry of the telemetry buffer (caller holds tel_mu).  Sets
+// no error text, so the stream thread can use it too.
+int tel_read_entry(rtc_loop* L, rtc_tel_record* rec, float* slopes, float* cmds, float* partials,
+                   int64_t timeout_us) {
     const auto deadline = Clock::now() + std::chrono::microseconds(timeout_us < 0 ? 0 : timeout_us);
     const uint64_t D = (uint64_t)L->tel_depth;
     for (;;) {
         const uint64_t w = __atomic_load_n(L->h_wcount, __ATOMIC_ACQUIRE);
         if (L->tel_next >= w) {
-            if (timeout_us >= 0 && Clock::now() >= deadline) return fail(L, RTC_ETIMEDOUT, "no new telemetry entry");
+            if (timeout_us >= 0 && Clock::now() >= deadline) return RTC_ETIMEDOUT;
             std::this_thread::sleep_for(std::chrono::microseconds(20));
             continue;
         }
@@ -1487,6 +1521,80 @@ int rtc_telemetry_read(rtc_loop* L, rtc_tel_record* rec, float* slopes, size_t n
         *rec = r;
         return RTC_OK;
     }
+}
+
+int rtc_telemetry_read(rtc_loop* L, rtc_tel_record* rec, float* slopes, size_t ns, float* cmds, size_t na,
+                       float* partials, size_t npartials, int64_t timeout_us) {
+    if (!L || !rec) return fail(L, RTC_EINVAL, "loop and rec are required");
+    if (!L->tel_depth) return fail(L, RTC_EINVAL, "loop has no telemetry buffer (tel_depth 0)");
+    if (L->tel_streaming) return fail(L, RTC_EINVAL, "a telemetry stream is reading the buffer");
+    if (slopes && (!(L->tel_streams & RTC_TEL_SLOPES) || ns != (size_t)L->ns))
+        return fail(L, RTC_EINVAL, "slopes not recorded, or ns wrong");
+    if (cmds && (!(L->tel_streams & RTC_TEL_COMMANDS) || na != (size_t)L->na))
+        return fail(L, RTC_EINVAL, "commands not recorded, or na wrong");
+    if (partials && (!(L->tel_streams & RTC_TEL_PARTIALS) || npartials != (size_t)L->nwfs * L->na))
+        return fail(L, RTC_EINVAL, "partial commands not recorded, or size not nwfs x na");
+    std::lock_guard<std::mutex> g(L->tel_mu);
+    const int rc = tel_read_entry(L, rec, slopes, cmds, partials, timeout_us);
+    if (rc == RTC_ETIMEDOUT) return fail(L, rc, "no new telemetry entry");
+    return rc;
+}
+
+int rtc_telemetry_stream_start(rtc_loop* L, int fd) {
+    if (!L) return fail(nullptr, RTC_EINVAL, "loop is NULL");
+    if (!L->tel_depth) return fail(L, RTC_EINVAL, "loop has no telemetry buffer (tel_depth 0)");
+    if (fd < 0) return fail(L, RTC_EINVAL, "bad file descriptor");
+    if (L->tel_streaming || L->tel_thread.joinable()) return fail(L, RTC_EINVAL, "a telemetry stream already runs");
+    L->tel_stats = rtc_tel_stream_stats{};
+    L->tel_stop = false;
+    L->tel_streaming = true;
+    L->tel_thread = std::thread([L, fd]() {
+        const bool sl = L->tel_streams & RTC_TEL_SLOPES, cm = L->tel_streams & RTC_TEL_COMMANDS,
+                   pa = L->tel_streams & RTC_TEL_PARTIALS;
+        const size_t nfl = (sl ? L->ns : 0) + (cm ? L->na : 0) + (pa ? (size_t)L->nwfs * L->na : 0);
+        std::vector<char> buf(sizeof(rtc_tel_record) + nfl * 4);
+        float* body = reinterpret_cast<float*>(buf.data() + sizeof(rtc_tel_record));
+        float* ps = body;
+        float* pc = ps + (sl ? L->ns : 0);
+        float* pp = pc + (cm ? L->na : 0);
+        for (;;) {
+            const bool stopping = L->tel_stop.load();
+            rtc_tel_record rec{};
+            int rc;
+            {
+                std::lock_guard<std::mutex> g(L->tel_mu);
+                rc = tel_read_entry(L, &rec, sl ? ps : nullptr, cm ? pc : nullptr, pa ? pp : nullptr,
+                                    stopping ? 0 : 50000);
+            }
+            if (rc != RTC_OK) {
+                if (stopping) break;        // everything published before the stop request is written
+                continue;
+            }
+            L->tel_stats.lost += rec.lost;
+            std::memcpy(buf.data(), &rec, sizeof(rec));
+            size_t off = 0;
+            while (off < buf.size()) {
+                const ssize_t n = ::write(fd, buf.data() + off, buf.size() - off);
+                if (n < 0) {
+                    if (errno == EINTR) continue;
+                    L->tel_stats.write_error = errno;
+                    return;
+                }
+                off += (size_t)n;
+            }
+            ++L->tel_stats.entries;
+            L->tel_stats.bytes += buf.size();
+        }
+    });
+    return RTC_OK;
+}
+
+int rtc_telemetry_stream_stop(rtc_loop* L, rtc_tel_stream_stats* stats) {
+    if (!L) return fail(nullptr, RTC_EINVAL, "loop is NULL");
+    if (!L->tel_thread.joinable()) return fail(L, RTC_EINVAL, "no telemetry stream runs");
+    stop_stream(L);
+    if (stats) *stats = L->tel_stats;
+    return RTC_OK;
 }
 
 int rtc_get_timing(rtc_loop* L, uint64_t frame_id, rtc_timing* out, int64_t timeout_us) {

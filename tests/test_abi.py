@@ -86,7 +86,7 @@ def test_structs_mirror_the_header_layout(rtc, tmp_path):
     if shutil.which("gcc") is None:
         pytest.skip("gcc not available")
     structs = [rtc.rtc_wfs, rtc.rtc_geometry, rtc.rtc_calib, rtc.rtc_cmat, rtc.rtc_polc, rtc.rtc_chunk,
-               rtc.rtc_timing, rtc.rtc_tel_record, rtc.rtc_update_desc, rtc.rtc_server_loop_info, rtc.rtc_info]
+               rtc.rtc_timing, rtc.rtc_tel_record, rtc.rtc_tel_stream_stats, rtc.rtc_update_desc, rtc.rtc_server_loop_info, rtc.rtc_info]
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "rtc.h"', "int main(void) {"]
     for st in structs:
         n = st.__name__

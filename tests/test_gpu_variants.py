@@ -285,3 +285,36 @@ def test_loop_without_telemetry_buffer_rejects_reads(rtc, torch_cuda):
     with rtc.Loop(cfg) as loop:
         with pytest.raises(rtc.RtcError, match="no telemetry buffer"):
             loop.telemetry_read(timeout_us=0)
+
+
+def test_telemetry_stream_to_a_file(rtc, torch_cuda, tmp_path):
+    cfg = ragged_global_config(seed=95)
+    frames = synth.draw_frames(cfg, 3, seed=96)
+    n = 40
+    path = tmp_path / "tel.bin"
+    with open(path, "wb") as fh, rtc.Loop(cfg, tel_depth=64, tel_streams=ALL_TEL) as loop:
+        loop.telemetry_stream_start(fh.fileno())
+        with pytest.raises(rtc.RtcError, match="stream"):
+            loop.telemetry_read(timeout_us=0)                  # the stream is the reader now
+        cmds = {}
+        for k in range(n):
+            loop.submit_frame(k + 1, frames[k % 3])
+            cmds[k + 1] = loop.get_commands(timeout_us=WAIT_US)[1]
+        loop.sync()
+        st = loop.telemetry_stream_stop()
+    na, ns, nw = cfg["na"], cfg["ns"], len(cfg["wfs"])
+    rec_bytes = 40 + 4 * (ns + na + nw * na)
+    assert st["entries"] == n and st["lost"] == 0 and st["write_error"] == 0 and st["bytes"] == n * rec_bytes
+    raw = path.read_bytes()
+    assert len(raw) == n * rec_bytes
+    ref = OracleLoop(cfg)
+    for k in range(n):
+        e = raw[k * rec_bytes:(k + 1) * rec_bytes]
+        index, fid, t_cmd, t_wr, lost = np.frombuffer(e[:40], np.uint64)
+        body = np.frombuffer(e[40:], np.float32)
+        s, a, p = body[:ns], body[ns:ns + na], body[ns + na:].reshape(nw, na)
+        s_ref, a_ref = ref.step(frames[k % 3])
+        assert index == k and fid == k + 1 and lost == 0 and t_wr >= t_cmd
+        assert np.array_equal(a, cmds[k + 1])
+        assert rel(s, s_ref) <= TOL_F32 and rel(a, a_ref) <= TOL_F32
+        assert rel(p, oracle_partials(cfg, s_ref)) <= TOL_F32
