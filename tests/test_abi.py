@@ -148,3 +148,21 @@ def test_explicit_polc_and_norm_validation_without_gpu(rtc):
     st.geo.wfs[0].norm = 2
     assert rtc.lib.rtc_footprint(C.byref(st.geo), C.byref(st.cal), C.byref(st.cm), C.byref(st.pol), C.byref(r),
                                  C.byref(p)) == rtc.RTC_EINVAL
+
+
+def test_wfs_count_limits_without_gpu(rtc):
+    import numpy as np
+    from paper_1903_01852_gb300 import synth
+    rng = np.random.default_rng(5)
+    wfs = [synth.sh_wfs(rng, 2, 4, 8, 8, 0.0) for _ in range(rtc.RTC_MAX_WFS)]
+    ns = sum(2 * synth.num_valid(w) for w in wfs)
+    cfg = dict(na=3, ns=ns, wfs=wfs, M=np.zeros((3, ns), np.float32), gain=0.5, leak=0.01)
+    assert rtc.footprint(cfg)[0] > 0
+    w17 = wfs + [synth.sh_wfs(rng, 2, 4, 8, 8, 0.0)]
+    with pytest.raises(ValueError):
+        rtc.footprint(dict(cfg, wfs=w17, M=np.zeros((3, ns + 8), np.float32)))
+    st = rtc.describe(cfg)
+    st.geo.nwfs = 0
+    r, p = C.c_uint64(), C.c_uint64()
+    assert rtc.lib.rtc_footprint(C.byref(st.geo), C.byref(st.cal), C.byref(st.cm), C.byref(st.pol), C.byref(r),
+                                 C.byref(p)) == rtc.RTC_EINVAL
