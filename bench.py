@@ -732,7 +732,8 @@ def variants_arm(args):
     (2) camera-paced MCAO FP32 latency while every frame's slopes, commands and per-WFS partial commands
         are recorded in the telemetry circular buffer and a library thread streams them to a file
         descriptor (Section 3.3), against the same loop without telemetry;
-    (3) local against global normalisation of the ELT pyramid, FP32 and BF16."""
+    (3) camera-paced MCAO latency against the number of row chunks (and column blocks) per LGS camera;
+    (4) local against global normalisation of the ELT pyramid, FP32 and BF16."""
     import torch
     from paper_1903_01852_gb300 import binding as rtc
     from paper_1903_01852_gb300 import synth
@@ -809,9 +810,25 @@ def variants_arm(args):
                                           "by the GPU into a 1000-entry page-locked circular buffer, drained by the "
                                           "library's stream thread (copy out of the buffer, write() to /dev/null)",
                             **tel}
+        # (3) pipelining depth: row chunks per LGS camera (= column blocks per LGS), FP32 and BF16
+        chunks = {}
+        bcfg = bf16_config(cfg, rtc, torch)
+        for nch in (4, 8, 16, 40):
+            for fmt, base in (("f32", cfg), ("bf16", bcfg)):
+                if fmt == "bf16" and nch not in (8, 16):
+                    continue
+                c = dict(base, wfs=[dict(w, nblocks=nch) if w["nsubx"] > 2 else w for w in base["wfs"]])
+                pl = [synth.chunk_plan(w, nch if w["nsubx"] > 2 else 1) for w in c["wfs"]]
+                with rtc.Loop(c, timing=True) as lp:
+                    lat, _ = run_host_path(lp, host, pl, n_paced, n_warm, sampler, 1, paced=True)
+                chunks[f"{nch}_{fmt}"] = stats(lat)
+        del bcfg
+        out["chunks"] = {"definition": "paced MCAO latency (last pixel in -> commands returned, 500 Hz, 1.6 ms "
+                                       "readout) with each LGS camera's frame in N row chunks and its slopes in N "
+                                       "column blocks; key N_format", **chunks}
         del cfg, frames, dev, host
         torch.cuda.empty_cache()
-        # (3) pyramid normalisation
+        # (4) pyramid normalisation
         pcfg = synth.make_config("elt_scao_pyramid")
         pframes = synth.draw_frames(pcfg, FRAME_RING, seed=3)
         pdev = dev_copy(pframes)
@@ -847,7 +864,7 @@ def main():
     ap.add_argument("--serving", action="store_true", help="serving mix (LTAO + MCAO + 2 SCAO) instead")
     ap.add_argument("--serving-seconds", type=float, default=4.0)
     ap.add_argument("--variants", action="store_true",
-                    help="POLC forms, telemetry streaming, pyramid normalisation instead")
+                    help="POLC forms, telemetry streaming, chunking depth, pyramid normalisation instead")
     ap.add_argument("--variant-frames", type=int, default=3000, help="paced frames per --variants case")
     ap.add_argument("--workload", default="mcao", help="configuration (profiling aid; the bench line is mcao)")
     ap.add_argument("--quick", action="store_true", help="profiling aid: only the unpaced loop")
