@@ -470,8 +470,23 @@ __device__ void finalise_tile(const FinaliseArgs& f, const float* __restrict__ p
     const int r = ft * kFinRows + lane;
     const int b0 = (seg * f.nblk) / kGemvWarps, b1 = ((seg + 1) * f.nblk) / kGemvWarps;
     float y = 0.f;
-    if (r < na)
-        for (int b = b0; b < b1; ++b) y += __ldcg(partial + (size_t)b * na + r);
+    if (r < na) {
+        // loads issued eight at a time, added in block order
+        int b = b0;
+        for (; b + 8 <= b1; b += 8) {
+            float v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = __ldcg(partial + (size_t)(b + k) * na + r);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) y += v[k];
+        }
+        float v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = b + k < b1 ? __ldcg(partial + (size_t)(b + k) * na + r) : 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (b + k < b1) y += v[k];
+    }
     red[seg][lane] = y;
     __syncthreads();
     if (seg == 0 && r < na) {
