@@ -27,6 +27,7 @@ import argparse
 import gc
 import hashlib
 import json
+import re
 import statistics
 import subprocess
 import sys
@@ -124,10 +125,20 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def kernel_source_hash():
+def code_text(src):
+    """Source text without comments and whitespace: what the compiler sees of it."""
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return re.sub(r"\s+", "", src)
+
+
+def kernel_source_hash(texts=None):
+    """Hash of the kernel sources (comments and whitespace ignored), recorded beside the
+    ncu figures so that they are reported only for the kernels they were taken on."""
     h = hashlib.sha256()
     for f in ("rtc_kernels.cu", "rtc_internal.h"):
-        h.update(open(os.path.join(ROOT, "paper_1903_01852_gb300", "csrc", f), "rb").read())
+        src = texts[f] if texts else open(os.path.join(ROOT, "paper_1903_01852_gb300", "csrc", f)).read()
+        h.update(code_text(src).encode())
     return h.hexdigest()[:16]
 
 

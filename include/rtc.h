@@ -8,12 +8,15 @@
  *   WFS pixels (streamed in row chunks, Section 2.1-2.2)
  *     -> calibration (dark subtraction, flat field, threshold; Section 2.2)
  *     -> Shack-Hartmann centre-of-gravity or pyramid quad-difference slopes
- *        (Fig. wfs_slopes, Section 2.2)
+ *        (Fig. wfs_slopes, Section 2.2; pyramid normalised locally or globally)
  *     -> reconstruction matrix-vector multiply, one partial per column block
  *        (Section 2.3; per-WFS partial DM commands summed by a master, Section 3)
- *     -> implicit pseudo-open-loop control term + leaky integrator
- *        (Section 3.4) -> DM commands, tagged with the camera frame number
- *        (Section 3, Fig. mcaoltao_test).
+ *     -> implicit (or explicit) pseudo-open-loop control term + leaky
+ *        integrator (Section 3.4) -> DM commands, tagged with the camera frame
+ *        number (Section 3, Fig. mcaoltao_test)
+ *     -> telemetry: per-frame slope ring and an optional circular buffer of
+ *        slopes, commands and per-WFS partial commands (Section 3.3); parameter
+ *        changes through a double buffer (Section 3.2).
  *
  * Conventions for every entry point:
  *   - Sizes are element counts unless a name ends in "pitch" (bytes).
@@ -25,7 +28,7 @@
  *     No C++ exception crosses the ABI.  The text of the last failure is
  *     available from rtc_last_error().
  *   - One thread submits to a loop; any thread may call rtc_get_commands,
- *     rtc_get_telemetry and rtc_get_timing.
+ *     rtc_get_telemetry, rtc_get_timing, rtc_telemetry_read and rtc_update.
  *
  * Slope order (the paper does not fix one): interleaved (x, y) per valid
  * unit, units in row-major order of the subaperture grid (SH) or of the pupil

@@ -7,7 +7,10 @@
 //                    matrix row, 128-bit streaming loads (Section 2.3: the MVM
 //                    is memory-bandwidth bound), with the finalisation (partial
 //                    sums + POLC term + leaky integrator, Section 3 and 3.4)
-//                    fused into its tail; also the POLC product P a
+//                    fused into its tail; also the POLC product P a (or D a in
+//                    explicit-POLC mode)
+//   normalise_kernel global normalisation of pyramid slopes by the mean flux
+//   telemetry_kernel one entry of the telemetry circular buffer (Section 3.3)
 //   pack / relayout / quantize / check kernels used at creation and for telemetry
 #include <algorithm>
 
