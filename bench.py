@@ -27,6 +27,7 @@ import argparse
 import gc
 import hashlib
 import json
+import platform
 import re
 import statistics
 import subprocess
@@ -395,6 +396,58 @@ def cpu_oracle(cfg, frames, nframes=3):
     return times, cmds, t_setup
 
 
+def oracle_stages(cfg, frames, nframes=5):
+    """Median per-frame time of each oracle step (the oracle's own functions, in the order
+    OracleLoop.step applies them): calibration + slopes of all WFS, the MVM, the control
+    law, the POLC product for the next frame."""
+    from oracle import rtc_oracle as orc
+    ref = orc.OracleLoop(cfg)
+    ref.step(frames[0])
+    rows = []
+    for k in range(nframes):
+        f = frames[(k + 1) % len(frames)]
+        t0 = time.perf_counter()
+        s = orc.frame_slopes(cfg, f)
+        t1 = time.perf_counter()
+        y = orc.mvm(ref.m, s)
+        t2 = time.perf_counter()
+        a = orc.control_step(ref.a, y, ref.q, cfg["gain"], cfg["leak"], cfg.get("clip"))
+        t3 = time.perf_counter()
+        q = ref.p @ a if ref.p is not None else ref.q
+        t4 = time.perf_counter()
+        ref.a, ref.q = a, q
+        rows.append([(t1 - t0) * 1e6, (t2 - t1) * 1e6, (t3 - t2) * 1e6, (t4 - t3) * 1e6, (t4 - t0) * 1e6])
+    med = np.median(np.array(rows), axis=0)
+    return {"slopes_us": float(med[0]), "mvm_us": float(med[1]), "control_us": float(med[2]),
+            "polc_us": float(med[3]), "frame_us": float(med[4]), "frames": nframes}
+
+
+def host_cpu():
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "model": model or platform.machine()}
+
+
+def oracle_stages_all_cores(nframes=5):
+    """oracle_stages in a child process whose BLAS uses every host core (the matrix
+    products parallelise over rows; the per-pixel steps stay on one thread)."""
+    n = os.cpu_count() or 1
+    env = dict(os.environ, OPENBLAS_NUM_THREADS=str(n), OMP_NUM_THREADS=str(n), MKL_NUM_THREADS=str(n))
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-stages", str(nframes)], env=env,
+                       capture_output=True, text=True, timeout=900)
+    if r.returncode != 0:
+        return {"error": r.stderr.strip().splitlines()[-1] if r.stderr.strip() else str(r.returncode)}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    d["threads"] = n
+    return d
+
+
 # ---------------------------------------------------------------------------- arms
 
 def max_over_ranks(vals, world, device):
@@ -544,6 +597,9 @@ def ours_arm(args, world, rank, local):
                     errs.append(float(np.max(np.abs(a - r)) / np.max(np.abs(r))))
         parity = {"frames": len(errs), "max_rel_err_commands": max(errs), "tol": 1e-5,
                   "norm": "max|a - a_oracle| / max|a_oracle| per frame, FP32 path, float64 oracle"}
+        cpu["stages_1_thread"] = oracle_stages(cfg, frames)
+        cpu["stages_all_cores"] = oracle_stages_all_cores()
+        cpu["host"] = host_cpu()
     for l in loops.values():
         l.close()
 
@@ -877,6 +933,7 @@ def main():
     ap.add_argument("--variants", action="store_true",
                     help="POLC forms, telemetry streaming, chunking depth, pyramid normalisation instead")
     ap.add_argument("--variant-frames", type=int, default=3000, help="paced frames per --variants case")
+    ap.add_argument("--oracle-stages", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--workload", default="mcao", help="configuration (profiling aid; the bench line is mcao)")
     ap.add_argument("--quick", action="store_true", help="profiling aid: only the unpaced loop")
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "e4m3"], help="matrix storage for --quick")
@@ -884,6 +941,10 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.oracle_stages:                    # child of oracle_stages_all_cores: host cores only, no GPU
+        cfg, frames = make_workload()
+        print(json.dumps(oracle_stages(cfg, frames, args.oracle_stages)), flush=True)
+        return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         reference_arm(args, world, rank)
