@@ -80,7 +80,7 @@ extern "C" {
                                   (twice the matrix memory) */
 #define RTC_FLAG_GRAPHS    16u /* page-locked input frames per ring slot and one captured CUDA
                                   graph per slot (rtc_next_frame_buffers, rtc_submit_frame_graph);
-                                  excludes RTC_FLAG_UPDATABLE */
+                                  excludes RTC_FLAG_UPDATABLE and RTC_FLAG_STAGE_TIMING */
 
 #define RTC_MAX_WFS 16
 
@@ -290,7 +290,10 @@ int rtc_get_telemetry(rtc_loop* loop, uint64_t frame_id, float* slopes, size_t n
  * the frame's first submitted work to the commands.  polc_us: the POLC
  * product after the commands.  slopes_us and mvm_us (the MVM kernel with its
  * fused finalisation) need RTC_FLAG_STAGE_TIMING, else they are -1;
- * final_us is 0 (the finalisation is part of the MVM kernel). */
+ * final_us is 0 (the finalisation is part of the MVM kernel).  In graph mode
+ * (RTC_FLAG_GRAPHS) latency_us and frame_us span the whole graph launch, POLC
+ * and telemetry included, and polc_us is about 0; RTC_FLAG_STAGE_TIMING is not
+ * available there. */
 typedef struct rtc_timing {
     uint64_t frame_id;
     float slopes_us, mvm_us, final_us, polc_us;
@@ -464,13 +467,17 @@ int rtc_server_destroy(rtc_server* server);
  * footprint exceeds the whole budget; creation errors as rtc_create. */
 int rtc_server_admit(rtc_server* server, const rtc_geometry* geometry, const rtc_calib* calib,
                      const rtc_cmat* cmat, const rtc_polc* polc, int32_t* loop_id);
-/* Destroy a loop (after its queued work) or drop it from the queue, then
- * create queued loops that now fit. */
+/* Destroy a loop (after its queued work and any rtc_server_submit for it that
+ * is in progress on another thread) or drop it from the queue, then create
+ * queued loops that now fit.  The loop's handle from rtc_server_loop is
+ * invalid afterwards. */
 int rtc_server_release(rtc_server* server, int32_t loop_id);
 /* The admitted loop's handle in *loop (NULL while queued), for
  * rtc_next_frame_buffers, rtc_get_commands, rtc_get_telemetry and the state calls. */
 int rtc_server_loop(rtc_server* server, int32_t loop_id, rtc_loop** loop);
-/* Launch the loop's next frame graph (rtc_submit_frame_graph) and track its latency. */
+/* Launch the loop's next frame graph (rtc_submit_frame_graph) and track its
+ * latency.  Different loops may be submitted from different threads; one
+ * thread at a time per loop. */
 int rtc_server_submit(rtc_server* server, int32_t loop_id, uint64_t frame_id);
 /* Latency statistics and admission state of a loop; reset != 0 clears the samples. */
 int rtc_server_stats(rtc_server* server, int32_t loop_id, int32_t reset, rtc_server_loop_info* out);

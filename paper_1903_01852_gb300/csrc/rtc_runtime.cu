@@ -412,6 +412,8 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
     L->tel_streams = G->tel_depth ? G->tel_streams : 0u;
     L->tel_decimate = G->tel_decimate > 0 ? G->tel_decimate : 1;
     if (L->graphs && L->updatable) return fail(L, RTC_EINVAL, "RTC_FLAG_GRAPHS and RTC_FLAG_UPDATABLE exclude each other");
+    if (L->graphs && L->stage_timing)
+        return fail(L, RTC_EINVAL, "RTC_FLAG_GRAPHS and RTC_FLAG_STAGE_TIMING exclude each other");
 
     // ---- slope-row and block plans ------------------------------------
     const int V = elems_per_16B(L->m_dtype);
@@ -953,7 +955,7 @@ TelArgs tel_args(rtc_loop* L) {
 int enqueue_tail(rtc_loop* L) {
     Slot& s = L->slots[L->cur_slot];
     float* cmd = L->d_ring + (size_t)L->cur_slot * L->slot_floats;
-    if (L->timing) TRY(record(L, s.ev_final, L->st));
+    if (L->timing && !L->capturing) TRY(record(L, s.ev_final, L->st));
     TRY(polc_product(L, !L->timing));
     TRY(record(L, s.ev_polc, L->st));
     if (L->telemetry || L->tel_depth) {
@@ -1176,7 +1178,7 @@ int submit_impl(rtc_loop* L, const rtc_chunk* c) {
 // captured frame graphs.
 int enqueue_whole_frame(rtc_loop* L, const FramePtrs& fp) {
     Slot& s = L->slots[L->cur_slot];
-    if (L->timing) {
+    if (L->timing && !L->capturing) {        // graph launches record these around the launch
         TRY(record(L, s.ev_start, L->st));
         TRY(record(L, s.ev_tail, L->st));
     }
@@ -1402,10 +1404,15 @@ int rtc_submit_frame_graph(rtc_loop* L, uint64_t frame_id) {
         status = RTC_EDROPPED;
     }
     TRY(begin_frame(L, frame_id, false));
+    Slot& s = L->slots[L->cur_slot];
+    if (L->timing) {                       // frame-level timing spans the whole graph launch
+        CK(L, cudaEventRecord(s.ev_start, L->st));
+        CK(L, cudaEventRecord(s.ev_tail, L->st));
+    }
     CK(L, cudaGraphLaunch(L->g_exec[L->cur_slot], L->st));
     // the graph ends with the telemetry joined back into the loop's stream: these
     // complete when the whole frame (POLC and telemetry included) has
-    Slot& s = L->slots[L->cur_slot];
+    if (L->timing) CK(L, cudaEventRecord(s.ev_final, L->st));
     CK(L, cudaEventRecord(s.ev_polc, L->st));
     CK(L, cudaEventRecord(s.ev_tel, L->st));
     CK(L, cudaEventRecord(L->ev_frame_end, L->st));

@@ -115,6 +115,7 @@ struct SLoop {
     uint64_t footprint = 0;
     bool admitted = false;
     bool creating = false;
+    int busy = 0;                        // submits in progress (under the server mutex)
     std::unique_ptr<OwnedDesc> desc;     // while queued
     std::deque<Inflight> inflight;
     std::vector<float> lat_us;
@@ -280,9 +281,16 @@ int rtc_server_release(rtc_server* S, int32_t loop_id) {
         if (it == S->loops.end()) return sfail(S, RTC_ENOENT, "no such loop");
         if (it->second->creating) return sfail(S, RTC_EINVAL, "loop is being created");
         l = std::move(it->second);
-        S->loops.erase(it);
+        S->loops.erase(it);              // no new submit can find it now
         if (l->admitted) S->used -= l->footprint;
         S->queue.erase(std::remove(S->queue.begin(), S->queue.end(), loop_id), S->queue.end());
+    }
+    for (;;) {                           // a submit that found the loop before the erase finishes first
+        {
+            std::lock_guard<std::mutex> g(S->mu);
+            if (l->busy == 0) break;
+        }
+        std::this_thread::yield();
     }
     if (l->L) rtc_destroy(l->L);     // waits for the loop's work, then frees its device memory
     admit_queued(S);
@@ -309,14 +317,16 @@ int rtc_server_submit(rtc_server* S, int32_t loop_id, uint64_t frame_id) {
         if (!it->second->admitted) return sfail(S, RTC_EINVAL, "loop not admitted yet");
         l = it->second.get();
         L = l->L;
+        ++l->busy;                       // rtc_server_release waits for it before destroying the loop
     }
     const auto t0 = Clock::now();
     const int rc = rtc_submit_frame_graph(L, frame_id);
-    if (rc != RTC_OK && rc != RTC_EDROPPED) return sfail(S, rc, rtc_last_error(L));
     Inflight f{};
-    rtc::loop_last_frame(L, &f.slot, &f.seq);
+    if (rc == RTC_OK || rc == RTC_EDROPPED) rtc::loop_last_frame(L, &f.slot, &f.seq);
     f.t_submit = t0;
     std::lock_guard<std::mutex> g(S->mu);
+    --l->busy;
+    if (rc != RTC_OK && rc != RTC_EDROPPED) return sfail(S, rc, rtc_last_error(L));
     l->inflight.push_back(f);
     return rc;
 }

@@ -166,3 +166,11 @@ def test_wfs_count_limits_without_gpu(rtc):
     r, p = C.c_uint64(), C.c_uint64()
     assert rtc.lib.rtc_footprint(C.byref(st.geo), C.byref(st.cal), C.byref(st.cm), C.byref(st.pol), C.byref(r),
                                  C.byref(p)) == rtc.RTC_EINVAL
+
+
+def test_graph_mode_excludes_stage_timing_without_gpu(rtc):
+    from paper_1903_01852_gb300 import synth
+    cfg = synth.make_config("scao_small")
+    assert rtc.footprint(cfg, flags=rtc.RTC_FLAG_GRAPHS | rtc.RTC_FLAG_TIMING)[0] > 0
+    with pytest.raises(rtc.RtcError, match="STAGE_TIMING"):
+        rtc.footprint(cfg, flags=rtc.RTC_FLAG_GRAPHS | rtc.RTC_FLAG_STAGE_TIMING)

@@ -117,3 +117,47 @@ def test_frame_ids_at_the_top_of_the_range(rtc, torch_cuda):
         run_pair(loop, cfg, frames, first_id=top)
         with pytest.raises(rtc.RtcError, match="EORDER"):
             loop.submit_frame(top, frames[0])          # not increasing
+
+
+def test_graph_mode_frame_timing_spans_the_launch(rtc, torch_cuda):
+    cfg = synth.make_config("scao_small", polc=True)
+    frames = synth.draw_frames(cfg, 3, seed=261)
+    with rtc.Loop(cfg, graphs=True, timing=True, telemetry=True, ring=2) as g, rtc.Loop(cfg) as d:
+        for k, f in enumerate(frames):
+            for b, x in zip(g.next_frame_buffers(), f):
+                b[:] = x
+            g.submit_graph(k + 1)
+            d.submit_frame(k + 1, f)
+            assert np.array_equal(g.get_commands(timeout_us=WAIT_US)[1], d.get_commands(timeout_us=WAIT_US)[1])
+            t = g.get_timing(k + 1, timeout_us=WAIT_US)
+            assert t["latency_us"] > 0 and t["frame_us"] >= t["latency_us"] and t["polc_us"] >= 0
+
+
+def test_server_release_while_another_thread_submits(rtc, torch_cuda):
+    import threading
+    import time
+    cfg = synth.make_config("scao_small")
+    budget = 2 * rtc.footprint(cfg, flags=rtc.RTC_FLAG_GRAPHS)[0]
+    with rtc.Server(budget) as srv:
+        lid = srv.admit(cfg)
+        errors, count = [], [0]
+
+        def submitter():
+            fid = 1
+            while True:
+                try:
+                    srv.submit(lid, fid)
+                except rtc.RtcError as e:
+                    if "ENOENT" not in str(e):
+                        errors.append(e)
+                    return
+                fid += 1
+                count[0] += 1
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        time.sleep(0.05)
+        srv.release(lid)                      # waits for a submit in progress, then destroys the loop
+        th.join(timeout=30)
+        assert not th.is_alive() and not errors and count[0] > 0
+        assert srv.usage()["used"] == 0
