@@ -423,15 +423,19 @@ def oracle_stages(cfg, frames, nframes=5):
 
 
 def host_cpu():
-    model = None
+    """Host core count and model (x86 'model name'; on Arm the implementer/part codes,
+    e.g. part 0xd4f is a Neoverse V2 core as in Grace)."""
+    info = {}
     try:
         for line in open("/proc/cpuinfo"):
-            if line.lower().startswith(("model name", "cpu part")):
-                model = line.split(":", 1)[1].strip()
-                break
+            key, _, val = line.partition(":")
+            key = key.strip().lower()
+            if key in ("model name", "cpu implementer", "cpu part") and key not in info:
+                info[key] = val.strip()
     except OSError:
         pass
-    return {"nproc": os.cpu_count(), "model": model or platform.machine()}
+    model = info.get("model name") or " ".join(f"{k} {info[k]}" for k in ("cpu implementer", "cpu part") if k in info)
+    return {"nproc": os.cpu_count(), "arch": platform.machine(), "model": model or None}
 
 
 def oracle_stages_all_cores(nframes=5):
