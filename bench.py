@@ -653,15 +653,20 @@ def ours_arm(args, world, rank, local):
     print(json.dumps(res), flush=True)
 
 
-def format_errors(args, frames, rtc, dev_frames, local, nframes=10):
+def format_errors(args, frames, rtc, dev_frames, local, nframes=100):
     """Slope and command errors of the GPU loop against the FP64 oracle, per frame, for this
     configuration and matrix format: against the oracle on the stored matrix (the parity check)
     and against the oracle on the float32 matrix (the cost of the format)."""
-    import copy
-    from oracle import OracleLoop
+    from oracle import OracleLoop, quantize_rows
     from paper_1903_01852_gb300 import synth
     base = synth.make_config(args.workload)
-    cfg = quant_config(base, rtc, __import__("torch"), args.dtype) if args.dtype != "f32" else base
+    cfg = dict(base)
+    if args.dtype != "f32":      # codes and scales from the oracle's quantiser feed both sides
+        codes, scale = quantize_rows(base["M"], args.dtype)
+        cfg.update(M=codes, M_scale=scale, M_dtype=args.dtype)
+        if base.get("P") is not None:
+            pc, ps = quantize_rows(base["P"], args.dtype)
+            cfg.update(P=pc, P_scale=ps, P_dtype=args.dtype)
     stored, true = OracleLoop(cfg), OracleLoop(base)
     out = {"frames": nframes, "slopes_vs_stored": 0.0, "cmds_vs_stored": 0.0, "cmds_vs_f32_matrix": 0.0}
     with rtc.Loop(cfg, device=local, telemetry=True) as loop:
@@ -700,7 +705,7 @@ def quick_arm(args, cfg, frames, rtc, torch, local):
     lat = stats([r["latency_us"] for r in rows])
     errors = None
     if args.errors:
-        errors = format_errors(args, frames, rtc, dev_frames, local)
+        errors = format_errors(args, frames, rtc, dev_frames, local, args.error_frames)
     mvm = statistics.median([r["mvm_us"] for r in srows])
     sl = statistics.median([r["slopes_us"] for r in srows])
     po = statistics.median([r["polc_us"] for r in srows])
@@ -942,6 +947,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="profiling aid: only the unpaced loop")
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "e4m3"], help="matrix storage for --quick")
     ap.add_argument("--errors", action="store_true", help="--quick: also errors against the FP64 oracle")
+    ap.add_argument("--error-frames", type=int, default=100, help="--errors: frames compared with the oracle")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

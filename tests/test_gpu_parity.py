@@ -285,13 +285,11 @@ def test_full_size_mcao_fp32_with_polc(rtc, torch_cuda, mcao):
 
 
 def test_full_size_mcao_bf16_against_stored_and_true_matrix(rtc, torch_cuda, mcao):
-    torch = torch_cuda
     cfg, frames = mcao
     q = copy.copy(cfg)
-    codes, scale = rtc.quantize_rows(torch.from_numpy(cfg["M"]).cuda(), "bf16")
-    pc, ps = rtc.quantize_rows(torch.from_numpy(cfg["P"]).cuda(), "bf16")
-    q.update(M=codes.cpu().numpy().view(np.uint16), M_scale=scale.cpu().numpy(), M_dtype="bf16",
-             P=pc.cpu().numpy().view(np.uint16), P_scale=ps.cpu().numpy(), P_dtype="bf16")
+    codes, scale = quantize_rows(cfg["M"], "bf16")          # the oracle's codes feed both sides
+    pc, ps = quantize_rows(cfg["P"], "bf16")
+    q.update(M=codes, M_scale=scale, M_dtype="bf16", P=pc, P_scale=ps, P_dtype="bf16")
     with rtc.Loop(q, telemetry=True) as loop:
         errs, cmds = run_pair(loop, q, frames, mode="device", nchunks=8)
     ref = OracleLoop(cfg)
