@@ -59,9 +59,14 @@ def pct(xs, q):
     return float(xs[lo] + (xs[hi] - xs[lo]) * (k - lo))
 
 
-def stats(xs):
-    return {"p50": pct(xs, 50), "p99": pct(xs, 99), "p999": pct(xs, 99.9), "mean": float(np.mean(xs)),
-            "jitter_rms": float(np.std(xs)), "max": float(np.max(xs)), "n": len(xs)}
+def stats(xs, period_us=None):
+    """Percentiles, mean, RMS jitter (standard deviation, the paper's "±") and max; with a
+    frame period, also the deadline misses (frames whose latency exceeded it)."""
+    out = {"p50": pct(xs, 50), "p99": pct(xs, 99), "p999": pct(xs, 99.9), "mean": float(np.mean(xs)),
+           "jitter_rms": float(np.std(xs)), "max": float(np.max(xs)), "n": len(xs)}
+    if period_us is not None:
+        out["deadline_misses"] = int(np.count_nonzero(np.asarray(xs) > period_us))
+    return out
 
 
 def peaks():
@@ -315,7 +320,7 @@ def run_host_path(loop, host_frames, plans, steps, warmup, sampler, first_id, pa
         th.join()
         return lat, fid, {"updates": len(upd_times), "swap_frames": len(swap_lat),
                           "upload_s_mean": float(np.mean(upd_times)) if upd_times else None,
-                          "latency_us_swap_frames": stats(swap_lat) if swap_lat else None}
+                          "latency_us_swap_frames": stats(swap_lat, 1e6 / PACED_HZ) if swap_lat else None}
     return lat, fid
 
 
@@ -568,11 +573,11 @@ def ours_arm(args, world, rank, local):
         for name in ("f32", "bf16"):
             lat, fid = run_host_path(loops[name], host_frames, plans, args.paced_frames, args.paced_warmup, sampler,
                                      fid, paced=True)
-            paced[name] = stats(lat)
+            paced[name] = stats(lat, 1e6 / PACED_HZ)
         # 4) the same paced FP32 loop while the whole control matrix is re-uploaded and swapped every second
         lat, fid, swap_info = run_host_path(loops["f32"], host_frames, plans, args.swap_frames, args.paced_warmup,
                                             sampler, fid, paced=True, swap=(1.0, {"M": cfg["M"]}))
-        swap_info["latency_us_other_frames"] = stats(lat)
+        swap_info["latency_us_other_frames"] = stats(lat, 1e6 / PACED_HZ)
         infos = {n: loops[n].info() for n in loops}
     finally:
         sampler.stop()
@@ -860,7 +865,7 @@ def variants_arm(args):
             polc_us = statistics.median([r["polc_us"] for r in rows])
             polc[name] = {"polc_product_us": polc_us, "polc_matrix_bytes": pbytes,
                           "polc_gbs": pbytes / (polc_us * 1e-6) / 1e9,
-                          "unpaced_frame_period_us": ms * 1000.0 / 300, "paced_latency_us": stats(lat)}
+                          "unpaced_frame_period_us": ms * 1000.0 / 300, "paced_latency_us": stats(lat, 1e6 / PACED_HZ)}
         del exp_cfg
         out["polc"] = {"definition": "polc_product_us: the POLC kernel after the command (stage timing, "
                                      "serialised); unpaced_frame_period_us: back-to-back frames from HBM; "
@@ -871,14 +876,14 @@ def variants_arm(args):
         all_streams = rtc.RTC_TEL_SLOPES | rtc.RTC_TEL_COMMANDS | rtc.RTC_TEL_PARTIALS
         with rtc.Loop(cfg, timing=True) as lp:
             lat, _ = run_host_path(lp, host, plans, n_paced, n_warm, sampler, 1, paced=True)
-            tel["without"] = stats(lat)
+            tel["without"] = stats(lat, 1e6 / PACED_HZ)
         with rtc.Loop(cfg, timing=True, tel_depth=1000, tel_streams=all_streams) as lp, \
                 open(os.devnull, "wb") as sink:
             lp.telemetry_stream_start(sink.fileno())
             lat, _ = run_host_path(lp, host, plans, n_paced, n_warm, sampler, 1, paced=True)
             lp.sync()
             st = lp.telemetry_stream_stop()
-            tel["with"] = stats(lat)
+            tel["with"] = stats(lat, 1e6 / PACED_HZ)
             tel["stream"] = st
             tel["entry_bytes"] = st["bytes"] // max(st["entries"], 1)
         out["telemetry"] = {"definition": "paced MCAO FP32, last pixel in -> commands returned; 'with': every "
@@ -897,7 +902,7 @@ def variants_arm(args):
                 pl = [synth.chunk_plan(w, nch if w["nsubx"] > 2 else 1) for w in c["wfs"]]
                 with rtc.Loop(c, timing=True) as lp:
                     lat, _ = run_host_path(lp, host, pl, n_paced, n_warm, sampler, 1, paced=True)
-                chunks[f"{nch}_{fmt}"] = stats(lat)
+                chunks[f"{nch}_{fmt}"] = stats(lat, 1e6 / PACED_HZ)
         del bcfg
         out["chunks"] = {"definition": "paced MCAO latency (last pixel in -> commands returned, 500 Hz, 1.6 ms "
                                        "readout) with each LGS camera's frame in N row chunks and its slopes in N "
