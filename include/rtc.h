@@ -396,6 +396,12 @@ int rtc_set_state(rtc_loop* loop, const float* a, size_t na);
 /* Wait for all queued work of the loop. */
 int rtc_sync(rtc_loop* loop);
 
+/* Memory-safety check for tests: every device and page-locked buffer the loop
+ * allocated ends in 256 guard bytes of a fixed pattern; after waiting for the
+ * loop's work, *corrupted receives the number of guard regions that anything
+ * (a kernel writing past a buffer, a copy) changed, 0 when all are intact. */
+int rtc_check_guards(rtc_loop* loop, int32_t* corrupted);
+
 /* The loop's CUDA stream (a cudaStream_t) in *stream, so a caller can order
  * its own work or timing events after the loop's; the loop keeps ownership. */
 int rtc_get_stream(rtc_loop* loop, void** stream);

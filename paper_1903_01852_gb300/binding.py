@@ -126,6 +126,7 @@ SIGNATURES = [
     ("rtc_get_state", C.c_int, [C.c_void_p, f32p, C.c_size_t]),
     ("rtc_set_state", C.c_int, [C.c_void_p, f32p, C.c_size_t]),
     ("rtc_sync", C.c_int, [C.c_void_p]),
+    ("rtc_check_guards", C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     ("rtc_get_stream", C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
     ("rtc_get_info", C.c_int, [C.c_void_p, C.POINTER(rtc_info)]),
     ("rtc_footprint", C.c_int, [C.POINTER(rtc_geometry), C.POINTER(rtc_calib), C.POINTER(rtc_cmat),
@@ -453,6 +454,12 @@ class Loop:
     def set_state(self, a):
         a = np.ascontiguousarray(a, dtype=np.float32)
         _check(lib.rtc_set_state(self._h, a.ctypes.data_as(f32p), self.na), self._h)
+
+    def check_guards(self):
+        """rtc_check_guards: number of buffer guard regions something overwrote (0 when intact)."""
+        n = C.c_int32()
+        _check(lib.rtc_check_guards(self._h, C.byref(n)), self._h)
+        return n.value
 
     def sync(self):
         _check(lib.rtc_sync(self._h), self._h)

@@ -95,6 +95,8 @@ struct rtc_loop {
     BlockDev* d_dblock = nullptr;
     float* d_u = nullptr;                   // explicit POLC: u = D a (ns, compact slope order)
     std::vector<void*> allocs;              // everything cudaMalloc'd, for destroy
+    // guard bytes after the end of every allocation (rtc_check_guards): start, host or device
+    std::vector<std::pair<unsigned char*, bool>> guards;
 
     // page-locked ring: per slot na commands then ns slopes
     float* h_ring = nullptr;
@@ -223,18 +225,42 @@ bool all_finite(const float* p, size_t n) {
     return true;
 }
 
+// Every allocation carries kGuardBytes of kGuardByte after its end; rtc_check_guards
+// reports any that a kernel (or a copy) overwrote.
+constexpr size_t kGuardBytes = 256;
+constexpr unsigned char kGuardByte = 0xA5;
+
 template <typename T>
 int dev_alloc(rtc_loop* L, T** p, size_t bytes) {
     void* v = nullptr;
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(&v, bytes);
+    bytes = round_up(bytes, 16);
+    cudaError_t e = cudaMalloc(&v, bytes + kGuardBytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(L, RTC_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
     }
     L->allocs.push_back(v);
-    L->device_bytes += bytes;
+    L->device_bytes += bytes + kGuardBytes;
+    unsigned char* g = static_cast<unsigned char*>(v) + bytes;
+    CK(L, cudaMemset(g, kGuardByte, kGuardBytes));
+    L->guards.emplace_back(g, false);
     *p = static_cast<T*>(v);
+    return RTC_OK;
+}
+
+// Page-locked, mapped host allocation with its guard bytes; *d: its device address.
+int pinned_alloc(rtc_loop* L, void** h, void** d, size_t bytes, const char* what) {
+    bytes = round_up(std::max<size_t>(bytes, 16), 16);
+    if (cudaHostAlloc(h, bytes + kGuardBytes, cudaHostAllocMapped) != cudaSuccess) {
+        cudaGetLastError();
+        *h = nullptr;
+        return fail(L, RTC_ENOMEM, std::string("page-locked ") + what + " of " + std::to_string(bytes) + " bytes");
+    }
+    unsigned char* g = static_cast<unsigned char*>(*h) + bytes;
+    std::memset(g, kGuardByte, kGuardBytes);
+    L->guards.emplace_back(g, true);
+    CK(L, cudaHostGetDevicePointer(d, *h, 0));
     return RTC_OK;
 }
 
@@ -755,34 +781,24 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
     // ---- page-locked ring, events -------------------------------------------
     L->slot_floats = round_up((size_t)L->na, 4) + round_up((size_t)L->ns, 4);
     {
-        void* h = nullptr;
-        cudaError_t e = cudaHostAlloc(&h, (size_t)L->ring * L->slot_floats * 4, cudaHostAllocMapped);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return fail(L, RTC_ENOMEM, "page-locked command ring");
-        }
+        void *h = nullptr, *d = nullptr;
+        const int rc = pinned_alloc(L, &h, &d, (size_t)L->ring * L->slot_floats * 4, "command ring");
         L->h_ring = static_cast<float*>(h);
+        TRY(rc);
         std::memset(L->h_ring, 0, (size_t)L->ring * L->slot_floats * 4);
-        void* d = nullptr;
-        CK(L, cudaHostGetDevicePointer(&d, h, 0));
         L->d_ring = static_cast<float*>(d);
     }
     {
-        void* h = nullptr;
+        void *h = nullptr, *d = nullptr;
         // per slot: completion word, its expected value, frame id; then the telemetry count
         const size_t words = 3 * (size_t)L->ring + 1;
-        cudaError_t e = cudaHostAlloc(&h, words * sizeof(unsigned long long), cudaHostAllocMapped);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return fail(L, RTC_ENOMEM, "page-locked completion words");
-        }
+        const int rc = pinned_alloc(L, &h, &d, words * sizeof(unsigned long long), "completion words");
         L->h_done = static_cast<unsigned long long*>(h);
+        TRY(rc);
         L->h_seq = L->h_done + L->ring;
         L->h_fid = L->h_seq + L->ring;
         L->h_wcount = L->h_fid + L->ring;
         std::memset(h, 0, words * sizeof(unsigned long long));
-        void* d = nullptr;
-        CK(L, cudaHostGetDevicePointer(&d, h, 0));
         L->d_done = static_cast<unsigned long long*>(d);
         L->d_seq = L->d_done + L->ring;
         L->d_fid = L->d_seq + L->ring;
@@ -798,15 +814,11 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
         if (L->tel_streams & RTC_TEL_PARTIALS) { L->tel_off_p = (int)off; off += r4((long long)L->nwfs * L->na); }
         L->tel_entry_floats = kTelHeaderFloats + off;
         const size_t bytes = (size_t)L->tel_depth * L->tel_entry_floats * 4;
-        void* h = nullptr;
-        if (cudaHostAlloc(&h, bytes, cudaHostAllocMapped) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(L, RTC_ENOMEM, "page-locked telemetry buffer of " + std::to_string(bytes) + " bytes");
-        }
+        void *h = nullptr, *d = nullptr;
+        const int rc = pinned_alloc(L, &h, &d, bytes, "telemetry buffer");
         L->h_tel = static_cast<float*>(h);
+        TRY(rc);
         std::memset(h, 0xff, bytes);          // no entry valid yet (index all ones)
-        void* d = nullptr;
-        CK(L, cudaHostGetDevicePointer(&d, h, 0));
         L->d_tel = static_cast<float*>(d);
         TRY(dev_alloc(L, &L->d_telctr, 3 * sizeof(unsigned long long)));
         CK(L, cudaMemset(L->d_telctr, 0, 3 * sizeof(unsigned long long)));
@@ -1202,16 +1214,12 @@ int capture_graphs(rtc_loop* L) {
     for (int slot = 0; slot < L->ring; ++slot) {
         FramePtrs fp{};
         for (int k = 0; k < L->nwfs; ++k) {
-            void* h = nullptr;
+            void *h = nullptr, *d = nullptr;
             const size_t bytes = (size_t)L->wfs[k].height * L->g_pitch[k];
-            if (cudaHostAlloc(&h, bytes, cudaHostAllocMapped) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(L, RTC_ENOMEM, "page-locked input frames");
-            }
-            std::memset(h, 0, bytes);
+            const int rc = pinned_alloc(L, &h, &d, bytes, "input frames");
             L->g_px[slot][k] = static_cast<uint16_t*>(h);
-            void* d = nullptr;
-            CK(L, cudaHostGetDevicePointer(&d, h, 0));
+            TRY(rc);
+            std::memset(h, 0, bytes);
             fp.px[k] = static_cast<const uint16_t*>(d);
             fp.pitch[k] = (long long)(L->g_pitch[k] / 2);
         }
@@ -1754,6 +1762,31 @@ int rtc_sync(rtc_loop* L) {
     for (cudaStream_t w : L->st_w) CK(L, cudaStreamSynchronize(w));
     CK(L, cudaStreamSynchronize(L->st));
     CK(L, cudaStreamSynchronize(L->st_tel));
+    return RTC_OK;
+}
+
+int rtc_check_guards(rtc_loop* L, int32_t* corrupted) {
+    if (!L || !corrupted) return fail(L, RTC_EINVAL, "loop and corrupted are required");
+    TRY(use_device(L));
+    for (cudaStream_t w : L->st_w) CK(L, cudaStreamSynchronize(w));
+    CK(L, cudaStreamSynchronize(L->st));
+    CK(L, cudaStreamSynchronize(L->st_tel));
+    if (L->st_up) CK(L, cudaStreamSynchronize(L->st_up));
+    int bad = 0;
+    unsigned char buf[kGuardBytes];
+    for (const auto& g : L->guards) {
+        const unsigned char* src = g.first;
+        if (!g.second) {
+            CK(L, cudaMemcpy(buf, g.first, kGuardBytes, cudaMemcpyDeviceToHost));
+            src = buf;
+        }
+        for (size_t i = 0; i < kGuardBytes; ++i)
+            if (src[i] != kGuardByte) {
+                ++bad;
+                break;
+            }
+    }
+    *corrupted = bad;
     return RTC_OK;
 }
 

@@ -50,4 +50,5 @@ def run_pair(loop, cfg, frames, mode="chunked", nchunks=8, first_id=1, check=Tru
             assert e[0] <= tol and e[1] <= tol, (k, e)
         errs.append(e)
         cmds.append(a)
+    assert loop.check_guards() == 0          # no kernel wrote past any of the loop's buffers
     return errs, cmds

@@ -99,3 +99,4 @@ def test_random_configuration(rtc, torch_cuda, seed):
             assert got == fid
             assert rel(s, s_ref) <= TOL_F32, (seed, k, "slopes", rel(s, s_ref))
             assert rel(a, a_ref) <= TOL_F32, (seed, k, "commands", rel(a, a_ref))
+        assert loop.check_guards() == 0          # no kernel wrote past any of the loop's buffers
