@@ -1,0 +1,55 @@
+"""Register and spill budgets of the hot kernels (CPU only: nvcc cross-compiles
+for sm_103a here).  The measured bandwidths depend on occupancy: the float32
+MVM runs 8 CTAs of 256 threads per SM only at <= 32 registers, the BF16 one 4
+at <= 64.  A source change that raises them shows here before it shows as a
+slower kernel on the GPU."""
+import os
+import re
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "paper_1903_01852_gb300", "csrc", "rtc_kernels.cu")
+
+# mangled entry -> (what, register budget)
+BUDGET = {
+    "_ZN3rtc11gemv_kernelILi0ELi4ELi1ELi4EEEvNS_8GemvArgsE": ("float32 MVM, 4 rows per warp", 32),
+    "_ZN3rtc11gemv_kernelILi0ELi4ELi1ELi2EEEvNS_8GemvArgsE": ("float32 MVM, 2 rows per warp", 32),
+    "_ZN3rtc11gemv_kernelILi1ELi2ELi4ELi4EEEvNS_8GemvArgsE": ("BF16 MVM", 64),
+    "_ZN3rtc11gemv_kernelILi2ELi1ELi4ELi4EEEvNS_8GemvArgsE": ("E4M3 MVM", 48),
+    "_ZN3rtc13slopes_kernelENS_9SlopeArgsE": ("slope kernel", 64),
+}
+
+
+def ptxas_report():
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    r = subprocess.run([nvcc, "-std=c++17", "-O3", "-gencode", "arch=compute_103a,code=sm_103a", "-Xptxas", "-v",
+                        "-I", os.path.join(ROOT, "include"), "-c", SRC, "-o", os.devnull],
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    report, entry = {}, None
+    for line in (r.stdout + r.stderr).splitlines():
+        m = re.search(r"Compiling entry function '(\w+)'", line)
+        if m:
+            entry = m.group(1)
+            continue
+        m = re.search(r"(\d+) bytes spill stores, (\d+) bytes spill loads", line)
+        if m and entry:
+            report.setdefault(entry, {})["spill"] = int(m.group(1)) + int(m.group(2))
+        m = re.search(r"Used (\d+) registers", line)
+        if m and entry:
+            report.setdefault(entry, {})["regs"] = int(m.group(1))
+    return report
+
+
+def test_hot_kernels_stay_within_their_register_budget_without_spills():
+    rep = ptxas_report()
+    for name, (what, budget) in BUDGET.items():
+        assert name in rep, f"{what}: entry {name} not compiled"
+        assert rep[name]["regs"] <= budget, f"{what}: {rep[name]['regs']} registers > {budget}"
+    spilling = {k: v["spill"] for k, v in rep.items() if v.get("spill")}
+    assert not spilling, spilling
