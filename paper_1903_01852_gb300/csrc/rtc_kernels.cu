@@ -506,7 +506,7 @@ __device__ void finalise_tile(const FinaliseArgs& f, const float* __restrict__ p
 }
 
 template <int DT, int U, int RI, int RPW>
-__global__ void __launch_bounds__(kGemvWarps * 32) gemv_kernel(const __grid_constant__ GemvArgs a) {
+__device__ __forceinline__ void gemv_body(const GemvArgs& a) {
     static_assert(RPW % RI == 0 && kFinRows % (kGemvWarps * RPW) == 0, "row tiling");
     __shared__ int s_last;
     const int bi = blockIdx.x / a.tiles;
@@ -596,6 +596,19 @@ __global__ void __launch_bounds__(kGemvWarps * 32) gemv_kernel(const __grid_cons
             }
         }
     }
+}
+
+template <int DT, int U, int RI, int RPW>
+__global__ void __launch_bounds__(kGemvWarps * 32) gemv_kernel(const __grid_constant__ GemvArgs a) {
+    gemv_body<DT, U, RI, RPW>(a);
+}
+
+// One row per warp: the launches over a single column block (the POLC product, a
+// row chunk's block) have about a thousand CTAs, and at <= 32 registers all of
+// them fit in one wave of eight CTAs per SM.
+template <int DT, int U, int RI>
+__global__ void __launch_bounds__(kGemvWarps * 32, 8) gemv_kernel_1row(const __grid_constant__ GemvArgs a) {
+    gemv_body<DT, U, RI, RI>(a);
 }
 
 // Telemetry entry of one frame: grid.y enumerates the recorded sections (one
@@ -704,7 +717,8 @@ cudaError_t launch_gemv_t(const GemvArgs& base, int nb, long long avg_row_bytes,
     a.prefetch_ctas = pdl ? (int)std::min<long long>(grid.x, (96LL << 20) / tile_bytes) : 0;
     if (rpw >= 4) return launch_maybe_pdl(gemv_kernel<DT, U, RI, (RI > 4 ? RI : 4)>, grid, a, pdl, st);
     if (rpw >= 2) return launch_maybe_pdl(gemv_kernel<DT, U, RI, (RI > 2 ? RI : 2)>, grid, a, pdl, st);
-    return launch_maybe_pdl(gemv_kernel<DT, U, RI, RI>, grid, a, pdl, st);
+    if constexpr (RI == 1) return launch_maybe_pdl(gemv_kernel_1row<DT, U, 1>, grid, a, pdl, st);
+    else return launch_maybe_pdl(gemv_kernel<DT, U, RI, RI>, grid, a, pdl, st);
 }
 
 cudaError_t launch_gemv(int dtype, const void* M, const BlockDev* blocks, int b0, int nb, int na, const float* x,

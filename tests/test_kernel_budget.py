@@ -2,7 +2,8 @@
 for sm_103a here).  The measured bandwidths depend on occupancy: the float32
 MVM runs 8 CTAs of 256 threads per SM only at <= 32 registers, the BF16 one 4
 at <= 64.  A source change that raises them shows here before it shows as a
-slower kernel on the GPU."""
+slower kernel on the GPU (a single-block float32 launch at 34 registers ran as
+1.03 waves, and the POLC product took 51 instead of 41 us)."""
 import os
 import re
 import shutil
@@ -13,13 +14,16 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "paper_1903_01852_gb300", "csrc", "rtc_kernels.cu")
 
-# mangled entry -> (what, register budget)
+# mangled entry -> (what, register budget, spill budget in bytes)
 BUDGET = {
-    "_ZN3rtc11gemv_kernelILi0ELi4ELi1ELi4EEEvNS_8GemvArgsE": ("float32 MVM, 4 rows per warp", 32),
-    "_ZN3rtc11gemv_kernelILi0ELi4ELi1ELi2EEEvNS_8GemvArgsE": ("float32 MVM, 2 rows per warp", 32),
-    "_ZN3rtc11gemv_kernelILi1ELi2ELi4ELi4EEEvNS_8GemvArgsE": ("BF16 MVM", 64),
-    "_ZN3rtc11gemv_kernelILi2ELi1ELi4ELi4EEEvNS_8GemvArgsE": ("E4M3 MVM", 48),
-    "_ZN3rtc13slopes_kernelENS_9SlopeArgsE": ("slope kernel", 64),
+    "_ZN3rtc11gemv_kernelILi0ELi4ELi1ELi4EEEvNS_8GemvArgsE": ("float32 MVM, 4 rows per warp", 32, 0),
+    "_ZN3rtc11gemv_kernelILi0ELi4ELi1ELi2EEEvNS_8GemvArgsE": ("float32 MVM, 2 rows per warp", 32, 0),
+    # one row per warp (single-block launches: the POLC product, a row chunk's block): held to
+    # 32 registers so that their ~1000 CTAs fit one wave; a few bytes of spill are the price
+    "_ZN3rtc16gemv_kernel_1rowILi0ELi4ELi1EEEvNS_8GemvArgsE": ("float32 MVM, 1 row per warp", 32, 32),
+    "_ZN3rtc11gemv_kernelILi1ELi2ELi4ELi4EEEvNS_8GemvArgsE": ("BF16 MVM", 64, 0),
+    "_ZN3rtc11gemv_kernelILi2ELi1ELi4ELi4EEEvNS_8GemvArgsE": ("E4M3 MVM", 48, 0),
+    "_ZN3rtc13slopes_kernelENS_9SlopeArgsE": ("slope kernel", 64, 0),
 }
 
 
@@ -48,8 +52,9 @@ def ptxas_report():
 
 def test_hot_kernels_stay_within_their_register_budget_without_spills():
     rep = ptxas_report()
-    for name, (what, budget) in BUDGET.items():
+    for name, (what, budget, spill) in BUDGET.items():
         assert name in rep, f"{what}: entry {name} not compiled"
         assert rep[name]["regs"] <= budget, f"{what}: {rep[name]['regs']} registers > {budget}"
-    spilling = {k: v["spill"] for k, v in rep.items() if v.get("spill")}
+        assert rep[name].get("spill", 0) <= spill, f"{what}: {rep[name]['spill']} bytes of spill > {spill}"
+    spilling = {k: v["spill"] for k, v in rep.items() if v.get("spill") and k not in BUDGET}
     assert not spilling, spilling
