@@ -551,9 +551,12 @@ def ours_arm(args, world, rank, local):
         cfgs = {"f32": cfg, "bf16": bcfg}
         for name in ("f32", "bf16"):
             # latency loops: the MVM starts while the slope kernel runs (frame-level events only)
-            loops[name] = rtc.Loop(cfgs[name], device=local, timing=True, telemetry=True, updatable=(name == "f32"))
+            loops[name] = rtc.Loop(cfgs[name], device=local, timing=True, telemetry=True)
             # stage loops: slope and MVM kernels timed separately (serialised) for the MVM bandwidth
             loops[name + "_stage"] = rtc.Loop(cfgs[name], device=local, stage_timing=True, telemetry=True)
+            # host-clock loops (paced and end-to-end): no CUDA events, whose records would add host
+            # time before the launches that matter
+            loops[name + "_host"] = rtc.Loop(cfgs[name], device=local, telemetry=True, updatable=(name == "f32"))
         fid = 1
         # 1) timed region: K unpaced steps, frames resident in HBM (device events around the region)
         ms_total, ids, _, fid = run_unpaced(loops["f32"], dev_frames, args.steps, args.warmup, torch, sampler, fid)
@@ -567,16 +570,16 @@ def ours_arm(args, world, rank, local):
         #    graph mode (the public path with the least host work), and rtc_process_frame
         with rtc.Loop(cfg, device=local, telemetry=True, graphs=True, ring=len(frames)) as gl:
             e2e_lat, _ = run_graph_frames(gl, frames, args.steps, args.warmup, sampler, 1)
-        pf_lat, fid = run_host_frames(loops["f32"], host_frames, args.steps, args.warmup, sampler, fid)
+        pf_lat, fid = run_host_frames(loops["f32_host"], host_frames, args.steps, args.warmup, sampler, fid)
         # 3) camera-paced last-pixel latency (the paper's definition), FP32 and BF16
         paced = {}
         for name in ("f32", "bf16"):
-            lat, fid = run_host_path(loops[name], host_frames, plans, args.paced_frames, args.paced_warmup, sampler,
-                                     fid, paced=True)
+            lat, fid = run_host_path(loops[name + "_host"], host_frames, plans, args.paced_frames, args.paced_warmup,
+                                     sampler, fid, paced=True)
             paced[name] = stats(lat, 1e6 / PACED_HZ)
         # 4) the same paced FP32 loop while the whole control matrix is re-uploaded and swapped every second
-        lat, fid, swap_info = run_host_path(loops["f32"], host_frames, plans, args.swap_frames, args.paced_warmup,
-                                            sampler, fid, paced=True, swap=(1.0, {"M": cfg["M"]}))
+        lat, fid, swap_info = run_host_path(loops["f32_host"], host_frames, plans, args.swap_frames,
+                                            args.paced_warmup, sampler, fid, paced=True, swap=(1.0, {"M": cfg["M"]}))
         swap_info["latency_us_other_frames"] = stats(lat, 1e6 / PACED_HZ)
         infos = {n: loops[n].info() for n in loops}
     finally:
@@ -634,7 +637,8 @@ def ours_arm(args, world, rank, local):
         "paced": {"definition": "last chunk submitted (last pixel in) -> commands returned, host clock; "
                                 f"{PACED_HZ:.0f} Hz, {READOUT_MS} ms readout over {NCHUNKS} row chunks per LGS camera, "
                                 f"pixels from page-locked host memory; {args.paced_frames} frames after "
-                                f"{args.paced_warmup} warm-up frames per format", **paced},
+                                f"{args.paced_warmup} warm-up frames per format; loops without CUDA event timing",
+                  **paced},
         "swap": {"definition": "paced FP32 frames while a second thread re-uploads the 1.67 GB control matrix "
                                "into the shadow buffer every 1 s (rtc_update); the first frame after each upload "
                                "swaps pointers at its start (Section 3.2's double buffer)", **swap_info},
@@ -861,7 +865,8 @@ def variants_arm(args):
                 pbytes = sl.info()["p_bytes"]
             with rtc.Loop(c, timing=True) as lp:
                 ms, _, _, fid = run_unpaced(lp, dev, 300, 20, torch, sampler, 1)
-                lat, _ = run_host_path(lp, host, plans, n_paced, n_warm, sampler, fid, paced=True)
+            with rtc.Loop(c) as lp:
+                lat, _ = run_host_path(lp, host, plans, n_paced, n_warm, sampler, 1, paced=True)
             polc_us = statistics.median([r["polc_us"] for r in rows])
             polc[name] = {"polc_product_us": polc_us, "polc_matrix_bytes": pbytes,
                           "polc_gbs": pbytes / (polc_us * 1e-6) / 1e9,
@@ -874,10 +879,10 @@ def variants_arm(args):
         # (2) telemetry streaming
         tel = {}
         all_streams = rtc.RTC_TEL_SLOPES | rtc.RTC_TEL_COMMANDS | rtc.RTC_TEL_PARTIALS
-        with rtc.Loop(cfg, timing=True) as lp:
+        with rtc.Loop(cfg) as lp:
             lat, _ = run_host_path(lp, host, plans, n_paced, n_warm, sampler, 1, paced=True)
             tel["without"] = stats(lat, 1e6 / PACED_HZ)
-        with rtc.Loop(cfg, timing=True, tel_depth=1000, tel_streams=all_streams) as lp, \
+        with rtc.Loop(cfg, tel_depth=1000, tel_streams=all_streams) as lp, \
                 open(os.devnull, "wb") as sink:
             lp.telemetry_stream_start(sink.fileno())
             lat, _ = run_host_path(lp, host, plans, n_paced, n_warm, sampler, 1, paced=True)
@@ -900,7 +905,7 @@ def variants_arm(args):
                     continue
                 c = dict(base, wfs=[dict(w, nblocks=nch) if w["nsubx"] > 2 else w for w in base["wfs"]])
                 pl = [synth.chunk_plan(w, nch if w["nsubx"] > 2 else 1) for w in c["wfs"]]
-                with rtc.Loop(c, timing=True) as lp:
+                with rtc.Loop(c) as lp:
                     lat, _ = run_host_path(lp, host, pl, n_paced, n_warm, sampler, 1, paced=True)
                 chunks[f"{nch}_{fmt}"] = stats(lat, 1e6 / PACED_HZ)
         del bcfg

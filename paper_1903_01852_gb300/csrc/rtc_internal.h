@@ -53,6 +53,14 @@ struct SlopePart {
     int pr0, pr1;             // pixel rows within the subaperture (SH); unused for pyramid rows
 };
 
+// Everything one slope-kernel CTA needs from the plan, read with one set of
+// 16-byte loads (the kernel is the first of a frame: a chain of dependent
+// table loads would sit in its latency).
+struct alignas(16) SlopeCta {
+    SlopeRow row;
+    SlopePart part;
+};
+
 constexpr int kFinRows = 32;  // rows per finalisation tile of the fused MVM tail
 
 // Fused finalisation of the reconstruction MVM (enabled for the control matrix).
@@ -136,12 +144,15 @@ cudaError_t launch_normalise(const int2* items, int item0, int nitems, int max_p
                              const WfsDev* wfs, const float* pscr, const float* ref, const float* pol, float* s_pad,
                              bool pdl, cudaStream_t st);
 
-// Slope kernel over the part table entries [part0, part0 + nparts).  Each slope
-// is (measured - ref) + pol, with ref and pol (compact slope order) optional.
-cudaError_t launch_slopes(const SlopePart* parts, int part0, int nparts, const SlopeRow* rows,
-                          const WfsDev* wfs, const FramePtrs& fp, const uint16_t* xlist,
-                          const float* ref, const float* pol, float* s_pad, float* pscr, unsigned* counters,
-                          int smem_bytes, cudaStream_t st);
+// Slope kernel over the CTA table entries [cta0, cta0 + nctas).  The WFS table
+// (nwfs entries, host memory) travels in the kernel parameters.  host_px: the
+// variant that keeps all of a thread's pixel rows in flight, for small launches
+// that read pixels in place from page-locked host memory.  Each slope is
+// (measured - ref) + pol, with ref and pol (compact slope order) optional.
+cudaError_t launch_slopes(const SlopeCta* ctas, int cta0, int nctas, const WfsDev* wfs, int nwfs,
+                          const FramePtrs& fp, bool host_px, const uint16_t* xlist, const float* ref,
+                          const float* pol, float* s_pad, float* pscr, unsigned* counters, int smem_bytes,
+                          cudaStream_t st);
 
 // GEMV over blocks [b0, b0 + nb): out[b * out_stride + r] = sum_j M_b[r][j] x[x_off_b + j],
 // times out_scale[r] when out_scale is not NULL; with fin, the CTA completing the

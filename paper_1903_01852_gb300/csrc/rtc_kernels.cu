@@ -44,6 +44,15 @@ __device__ __forceinline__ unsigned long long global_time_ns() {
     return t;
 }
 
+// Release/acquire fences (lighter than the sequentially consistent __threadfence).
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ void fence_acq_rel_sys() { asm volatile("fence.acq_rel.sys;" ::: "memory"); }
+
+// Prefetch of one line into L1 (no register is held for it).
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p) : "memory");
+}
+
 // Bulk prefetch of a contiguous, 16-byte aligned region into L2 (TMA engine).
 __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
@@ -59,13 +68,24 @@ __device__ __forceinline__ float calibrate(unsigned raw, float dark, float flat,
     return mode == RTC_THRESH_SUBTRACT ? __fsub_rn(c, T) : c;
 }
 
-// A slope pair as stored: (measured - reference) + pseudo-open-loop term.
-__device__ __forceinline__ void store_pair(float* __restrict__ s_pad, int pad, const float* __restrict__ ref,
-                                           const float* __restrict__ pol, int comp, float sx, float sy) {
-    if (ref) { sx -= ref[comp]; sy -= ref[comp + 1]; }
-    if (pol) { sx += pol[comp]; sy += pol[comp + 1]; }
+// A slope pair as stored: (measured - reference) + pseudo-open-loop term, with
+// the reference (r) and pseudo-open-loop (p) pairs already loaded.
+__device__ __forceinline__ void store_pair_v(float* __restrict__ s_pad, int pad, bool has_ref, float2 r, bool has_pol,
+                                             float2 p, float sx, float sy) {
+    if (has_ref) { sx -= r.x; sy -= r.y; }
+    if (has_pol) { sx += p.x; sy += p.y; }
     s_pad[pad] = sx;
     s_pad[pad + 1] = sy;
+}
+
+// The reference or pseudo-open-loop pair of compact slope index comp (zero when absent).
+__device__ __forceinline__ float2 load_pair(const float* __restrict__ v, int comp) {
+    return v ? make_float2(v[comp], v[comp + 1]) : make_float2(0.f, 0.f);
+}
+
+__device__ __forceinline__ void store_pair(float* __restrict__ s_pad, int pad, const float* __restrict__ ref,
+                                           const float* __restrict__ pol, int comp, float sx, float sy) {
+    store_pair_v(s_pad, pad, ref != nullptr, load_pair(ref, comp), pol != nullptr, load_pair(pol, comp), sx, sy);
 }
 
 // SH slope-row part: pixel rows [pr0, pr1) of one subaperture row.  The CTA
@@ -75,7 +95,18 @@ __device__ __forceinline__ void store_pair(float* __restrict__ s_pad, int pad, c
 // subaperture adds its npx columns (one thread per subaperture when that sum is
 // short, one warp otherwise).  A row split in several parts (large
 // subapertures) publishes per-part sums; the last part to finish adds them in
-// part order and writes the slopes.  Every sum has a fixed order.
+// part order and writes the slopes.  Every sum has a fixed order.  The table
+// entries of each thread's (or warp's) first subaperture are loaded before the
+// column sums, so they are not a dependent load at the end.
+// kAllRows (row chunks read in place over the CPU-GPU link, whose latency is
+// several times that of HBM): a thread first issues the loads of all its pixel
+// rows (up to kRowsInFlight), then calibrates them four rows at a time; the
+// additions keep the same order, so the slopes are bit-identical to the other
+// variant.  It takes ~160 registers (one CTA per SM): right for a chunk's few
+// dozen CTAs, not for a whole frame's hundreds.
+constexpr int kRowsInFlight = 12;
+
+template <bool kAllRows>
 __device__ void sh_part(const SlopePart& P, const SlopeRow& row, const WfsDev& W, const uint16_t* __restrict__ px,
                         long long pitch, int prow0, const uint16_t* __restrict__ xlist, const float* __restrict__ ref,
                         const float* __restrict__ pol, float* __restrict__ s_pad, float* __restrict__ pscr,
@@ -94,6 +125,18 @@ __device__ void sh_part(const SlopePart& P, const SlopeRow& row, const WfsDev& W
     const float half = 0.5f * float(n - 1);
     const float T = W.threshold;
     const int mode = W.thresh_mode;
+    const bool single = row.nparts == 1;
+    const bool by_thread = n * G <= 64;
+    const int u_first = by_thread ? (int)threadIdx.x : (int)(threadIdx.x >> 5);
+    int x_first = 0;
+    float2 r_first = make_float2(0.f, 0.f), p_first = make_float2(0.f, 0.f);
+    if (u_first < row.nunits) {
+        x_first = xlist[row.unit0 + u_first];
+        if (single) {
+            r_first = load_pair(ref, row.s_compact + 2 * u_first);
+            p_first = load_pair(pol, row.s_compact + 2 * u_first);
+        }
+    }
 
     for (int idx = threadIdx.x; idx < nq * G; idx += blockDim.x) {
         const int q = idx % nq;
@@ -102,6 +145,43 @@ __device__ void sh_part(const SlopePart& P, const SlopeRow& row, const WfsDev& W
         float F[4] = {0.f, 0.f, 0.f, 0.f};
         float Y[4] = {0.f, 0.f, 0.f, 0.f};
         int r = P.pr0 + g;
+        if constexpr (kAllRows) {
+            uint2 rw[kRowsInFlight];
+#pragma unroll
+            for (int j = 0; j < kRowsInFlight; ++j) {
+                const int rr = r + j * G;
+                if (rr < P.pr1)
+                    rw[j] = __ldg(reinterpret_cast<const uint2*>(px + ((long long)y0 + rr - prow0) * pitch + xa));
+            }
+#pragma unroll
+            for (int j0 = 0; j0 < kRowsInFlight; j0 += 4) {
+                float4 d[4], f[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const long long yy = y0 + r + (j0 + k) * G;
+                    if (r + (j0 + k) * G < P.pr1) {
+                        d[k] = __ldg(reinterpret_cast<const float4*>(W.dark + yy * W.calib_pitch + xa));
+                        f[k] = __ldg(reinterpret_cast<const float4*>(W.flat + yy * W.calib_pitch + xa));
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int rr = r + (j0 + k) * G;
+                    if (rr < P.pr1) {
+                        const uint2 q2 = rw[j0 + k];
+                        const float yc = float(rr) - half;
+                        const float t0 = calibrate(q2.x & 0xffffu, d[k].x, f[k].x, T, mode);
+                        const float t1 = calibrate(q2.x >> 16, d[k].y, f[k].y, T, mode);
+                        const float t2 = calibrate(q2.y & 0xffffu, d[k].z, f[k].z, T, mode);
+                        const float t3 = calibrate(q2.y >> 16, d[k].w, f[k].w, T, mode);
+                        F[0] += t0; F[1] += t1; F[2] += t2; F[3] += t3;
+                        Y[0] = fmaf(t0, yc, Y[0]); Y[1] = fmaf(t1, yc, Y[1]);
+                        Y[2] = fmaf(t2, yc, Y[2]); Y[3] = fmaf(t3, yc, Y[3]);
+                    }
+                }
+            }
+            r += kRowsInFlight * G;    // rows beyond (never with the create-time part split) go below
+        }
         for (; r + 3 * G < P.pr1; r += 4 * G) {
             uint2 rw[4];
             float4 d[4], f[4];
@@ -146,20 +226,22 @@ __device__ void sh_part(const SlopePart& P, const SlopeRow& row, const WfsDev& W
     }
     __syncthreads();
 
-    const bool single = row.nparts == 1;
     auto emit = [&](int u, float Fs, float Xs, float Ys) {
         if (single) {
             float sx = 0.f, sy = 0.f;
             if (Fs > 0.f) { sx = Xs / Fs; sy = Ys / Fs; }
-            store_pair(s_pad, row.s_pad + 2 * u, ref, pol, row.s_compact + 2 * u, sx, sy);
+            if (u == u_first)
+                store_pair_v(s_pad, row.s_pad + 2 * u, ref != nullptr, r_first, pol != nullptr, p_first, sx, sy);
+            else
+                store_pair(s_pad, row.s_pad + 2 * u, ref, pol, row.s_compact + 2 * u, sx, sy);
         } else {
             float* o = pscr + row.pscr + 3 * ((size_t)P.part * row.nunits + u);
             o[0] = Fs; o[1] = Xs; o[2] = Ys;
         }
     };
-    if (n * G <= 64) {
+    if (by_thread) {
         for (int u = threadIdx.x; u < row.nunits; u += blockDim.x) {
-            const int cx = xlist[row.unit0 + u] * n;
+            const int cx = (u == u_first ? x_first : xlist[row.unit0 + u]) * n;
             float Fs = 0.f, Xs = 0.f, Ys = 0.f;
             for (int k = 0; k < n; ++k) {
                 float fc = 0.f, yc = 0.f;
@@ -173,7 +255,7 @@ __device__ void sh_part(const SlopePart& P, const SlopeRow& row, const WfsDev& W
     } else {
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
         for (int u = warp; u < row.nunits; u += nw) {
-            const int cx = xlist[row.unit0 + u] * n;
+            const int cx = (u == u_first ? x_first : xlist[row.unit0 + u]) * n;
             float Fs = 0.f, Xs = 0.f, Ys = 0.f;
             for (int p = lane; p < n * G; p += 32) {
                 const int k = p % n, g = p / n;
@@ -189,13 +271,17 @@ __device__ void sh_part(const SlopePart& P, const SlopeRow& row, const WfsDev& W
         }
     }
     if (single) return;
-    // last part of the row to finish adds the parts in order
-    __threadfence();
+    // last part of the row to finish adds the parts in order (release and
+    // acquire by thread 0, ordered with the other threads by the barriers)
     __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&counters[P.row], 1u) == (unsigned)(row.nparts - 1);
+    if (threadIdx.x == 0) {
+        fence_acq_rel_gpu();
+        const bool last = atomicAdd(&counters[P.row], 1u) == (unsigned)(row.nparts - 1);
+        if (last) fence_acq_rel_gpu();
+        s_last = last;
+    }
     __syncthreads();
     if (!s_last) return;
-    __threadfence();
     for (int u = threadIdx.x; u < row.nunits; u += blockDim.x) {
         float Fs = 0.f, Xs = 0.f, Ys = 0.f;
         for (int k = 0; k < row.nparts; ++k) {
@@ -259,32 +345,42 @@ __device__ void pyr_row(const SlopeRow& row, const WfsDev& W, const uint16_t* __
     }
 }
 
+// The WFS table travels in the parameters (constant bank), so a CTA's only
+// global load before its pixels is its own 48-byte table entry.
 struct SlopeArgs {
-    const SlopePart* parts;
-    int part0;
-    const SlopeRow* rows;
-    const WfsDev* wfs;
-    FramePtrs fp;
+    const SlopeCta* ctas;
+    int cta0;
     const uint16_t* xlist;
     const float* ref;
     const float* pol;
     float* s_pad;
     float* pscr;
     unsigned* counters;
+    FramePtrs fp;
+    WfsDev wfs[kMaxWfs];
 };
+static_assert(sizeof(SlopeCta) == 48, "slope CTA entry is three 16-byte vectors");
+static_assert(sizeof(SlopeArgs) <= 4096, "slope kernel parameters");
 
+template <bool kAllRows>
 __global__ void __launch_bounds__(kSlopeThreads) slopes_kernel(const __grid_constant__ SlopeArgs a) {
     extern __shared__ float sm[];
     pdl_trigger();        // the MVM may launch now and prefetch its matrix tiles while slopes run
-    const SlopePart P = a.parts[a.part0 + blockIdx.x];
-    const SlopeRow row = a.rows[P.row];
-    const WfsDev W = a.wfs[row.wfs];
+    union {
+        int4 v[3];
+        SlopeCta c;
+    } e;
+    const int4* src = reinterpret_cast<const int4*>(a.ctas + a.cta0 + blockIdx.x);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) e.v[k] = __ldg(src + k);
+    const SlopeRow& row = e.c.row;
+    const int w = row.wfs;
+    const WfsDev& W = a.wfs[w];
     if (W.kind == RTC_WFS_SH)
-        sh_part(P, row, W, a.fp.px[row.wfs], a.fp.pitch[row.wfs], a.fp.row0[row.wfs], a.xlist, a.ref, a.pol, a.s_pad,
-                a.pscr, a.counters, sm);
+        sh_part<kAllRows>(e.c.part, row, W, a.fp.px[w], a.fp.pitch[w], a.fp.row0[w], a.xlist, a.ref, a.pol, a.s_pad, a.pscr,
+                a.counters, sm);
     else
-        pyr_row(row, W, a.fp.px[row.wfs], a.fp.pitch[row.wfs], a.fp.row0[row.wfs], a.xlist, a.ref, a.pol, a.s_pad,
-                a.pscr);
+        pyr_row(row, W, a.fp.px[w], a.fp.pitch[w], a.fp.row0[w], a.xlist, a.ref, a.pol, a.s_pad, a.pscr);
 }
 
 // Global normalisation of pyramid slopes, a programmatic dependent of the slope
@@ -345,15 +441,33 @@ cudaError_t launch_normalise(const int2* items, int item0, int nitems, int max_p
 
 cudaError_t configure_slopes(int smem_bytes) {
     if (smem_bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(slopes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    const cudaError_t e = cudaFuncSetAttribute(slopes_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               smem_bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(slopes_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
 }
 
-cudaError_t launch_slopes(const SlopePart* parts, int part0, int nparts, const SlopeRow* rows, const WfsDev* wfs,
-                          const FramePtrs& fp, const uint16_t* xlist, const float* ref, const float* pol,
-                          float* s_pad, float* pscr, unsigned* counters, int smem_bytes, cudaStream_t st) {
-    if (nparts <= 0) return cudaSuccess;
-    SlopeArgs a{parts, part0, rows, wfs, fp, xlist, ref, pol, s_pad, pscr, counters};
-    slopes_kernel<<<nparts, kSlopeThreads, smem_bytes, st>>>(a);
+cudaError_t launch_slopes(const SlopeCta* ctas, int cta0, int nctas, const WfsDev* wfs, int nwfs,
+                          const FramePtrs& fp, bool host_px, const uint16_t* xlist, const float* ref,
+                          const float* pol, float* s_pad, float* pscr, unsigned* counters, int smem_bytes,
+                          cudaStream_t st) {
+    if (nctas <= 0) return cudaSuccess;
+    if (nwfs < 1 || nwfs > kMaxWfs) return cudaErrorInvalidValue;
+    SlopeArgs a{};
+    a.ctas = ctas;
+    a.cta0 = cta0;
+    a.xlist = xlist;
+    a.ref = ref;
+    a.pol = pol;
+    a.s_pad = s_pad;
+    a.pscr = pscr;
+    a.counters = counters;
+    a.fp = fp;
+    std::copy(wfs, wfs + nwfs, a.wfs);
+    if (host_px)
+        slopes_kernel<true><<<nctas, kSlopeThreads, smem_bytes, st>>>(a);
+    else
+        slopes_kernel<false><<<nctas, kSlopeThreads, smem_bytes, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -466,12 +580,18 @@ struct GemvArgs {
 // The master's finalisation of one tile of kFinRows rows (Section 3: sum the
 // partial commands; Section 3.4: add the implicit-POLC term; leaky integrator).
 // Eight thread groups each add a contiguous range of blocks in block order,
-// then the eight group sums are added in group order.
+// then the eight group sums are added in group order.  The row's scale, POLC
+// term and state are prefetched into L1 while the partials load.
 __device__ void finalise_tile(const FinaliseArgs& f, const float* __restrict__ partial, int na, int ft) {
     __shared__ float red[kGemvWarps][32];
     const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
     const int r = ft * kFinRows + lane;
     const int b0 = (seg * f.nblk) / kGemvWarps, b1 = ((seg + 1) * f.nblk) / kGemvWarps;
+    if (seg == 0 && r < na) {
+        if (f.scale) prefetch_l1(f.scale + r);
+        prefetch_l1(f.q + r);
+        prefetch_l1(f.a + r);
+    }
     float y = 0.f;
     if (r < na) {
         // loads issued eight at a time, added in block order
@@ -567,30 +687,33 @@ __device__ __forceinline__ void gemv_body(const GemvArgs& a) {
     if (!a.fin.enabled) return;
     // Fused finalisation: the CTA that completes the last block of a row tile
     // (counted in rows, across launches of the same frame) finalises it.
-    __threadfence();
+    // Release/acquire through one thread: the barrier orders the CTA's partial
+    // stores before thread 0's release fence, and its acquire fence before the
+    // other threads' loads (fences are cumulative over the barrier).
     __syncthreads();
     const int ft = r0 / kFinRows;
     if (threadIdx.x == 0) {
         const int rows_here = min(r0 + kGemvWarps * RPW, a.na) - r0;
         const int ft_rows = min(kFinRows, a.na - ft * kFinRows);
+        fence_acq_rel_gpu();
         const unsigned prev = atomicAdd(&a.fin.counters[ft], (unsigned)rows_here);
-        s_last = prev + rows_here == (unsigned)(a.fin.nblk * ft_rows);
+        const bool last = prev + rows_here == (unsigned)(a.fin.nblk * ft_rows);
+        if (last) fence_acq_rel_gpu();
+        s_last = last;
     }
     __syncthreads();
     if (!s_last) return;
-    __threadfence();
     finalise_tile(a.fin, a.out, a.na, ft);
-    // commands of this tile visible to the host before the tile counts as done
-    __threadfence_system();
     __syncthreads();
     if (threadIdx.x == 0) {
         a.fin.counters[ft] = 0u;
         if (a.fin.done_flag) {
             const int nfin = (a.na + kFinRows - 1) / kFinRows;
+            fence_acq_rel_sys();    // this tile's commands reach the host before the tile counts as done
             if (atomicAdd(a.fin.tiles_done, 1u) == (unsigned)(nfin - 1)) {
                 *a.fin.tiles_done = 0u;
                 if (a.fin.t_done) *a.fin.t_done = global_time_ns();
-                __threadfence_system();
+                fence_acq_rel_sys();
                 const unsigned long long seq = *reinterpret_cast<const volatile unsigned long long*>(a.fin.seq);
                 *reinterpret_cast<volatile unsigned long long*>(a.fin.done_flag) = seq;
             }

@@ -76,8 +76,7 @@ struct rtc_loop {
     BlockDev* d_pblock = nullptr;
     std::vector<float*> d_dark, d_flat;
     WfsDev* d_wfs = nullptr;
-    SlopeRow* d_rows = nullptr;
-    SlopePart* d_parts = nullptr;
+    SlopeCta* d_ctas = nullptr;             // slope-kernel CTA table (row and part of each CTA)
     float* d_pscr = nullptr;                // per-part subaperture sums of split rows
     unsigned* d_row_cnt = nullptr;          // per slope row: parts finished
     unsigned* d_fin_cnt = nullptr;          // per finalisation tile: rows finished over blocks
@@ -747,10 +746,15 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
         L->upd_dark.assign(L->nwfs, 0);
         L->upd_flat.assign(L->nwfs, 0);
     }
-    TRY(dev_alloc(L, &L->d_rows, rows.size() * sizeof(SlopeRow)));
-    CK(L, cudaMemcpy(L->d_rows, rows.data(), rows.size() * sizeof(SlopeRow), cudaMemcpyHostToDevice));
-    TRY(dev_alloc(L, &L->d_parts, parts.size() * sizeof(SlopePart)));
-    CK(L, cudaMemcpy(L->d_parts, parts.data(), parts.size() * sizeof(SlopePart), cudaMemcpyHostToDevice));
+    {
+        std::vector<SlopeCta> ctas(parts.size());
+        for (size_t i = 0; i < parts.size(); ++i) {
+            ctas[i].row = rows[parts[i].row];
+            ctas[i].part = parts[i];
+        }
+        TRY(dev_alloc(L, &L->d_ctas, ctas.size() * sizeof(SlopeCta)));
+        CK(L, cudaMemcpy(L->d_ctas, ctas.data(), ctas.size() * sizeof(SlopeCta), cudaMemcpyHostToDevice));
+    }
     TRY(dev_alloc(L, &L->d_pscr, std::max<size_t>(pscr_floats, 4) * 4));
     TRY(dev_alloc(L, &L->d_row_cnt, (size_t)L->nrows * sizeof(unsigned)));
     CK(L, cudaMemset(L->d_row_cnt, 0, (size_t)L->nrows * sizeof(unsigned)));
@@ -1037,11 +1041,13 @@ FinaliseArgs fin_args(rtc_loop* L) {
     return f;
 }
 
-int slopes_rows(rtc_loop* L, int r0, int r1, const FramePtrs& fp, cudaStream_t st) {
+// host_px: the pixels are read in place from page-locked host memory (a row chunk):
+// the slope kernel variant with all of a thread's pixel rows in flight.
+int slopes_rows(rtc_loop* L, int r0, int r1, const FramePtrs& fp, bool host_px, cudaStream_t st) {
     const int p0 = L->part_start[r0], p1 = L->part_start[r1];
     const float* pol = L->explicit_polc ? L->d_u : nullptr;
-    CK(L, launch_slopes(L->d_parts, p0, p1 - p0, L->d_rows, L->d_wfs, fp, L->d_xlist, L->d_ref, pol, L->d_s,
-                        L->d_pscr, L->d_row_cnt, L->smem_bytes, st));
+    CK(L, launch_slopes(L->d_ctas, p0, p1 - p0, L->wfs_host.data(), L->nwfs, fp, host_px, L->d_xlist, L->d_ref, pol,
+                        L->d_s, L->d_pscr, L->d_row_cnt, L->smem_bytes, st));
     // globally normalised pyramids whose rows all ran here (they are never split across launches)
     int i0 = -1, i1 = -1;
     for (int k = 0; k < L->nwfs; ++k)
@@ -1069,14 +1075,15 @@ int reset_counters(rtc_loop* L) {
 }
 
 // Device address through which kernels can read p in place: device or managed
-// memory, or page-locked host memory (read over the CPU-GPU link); NULL for
-// pageable memory, which must be copied.
-const void* device_view(const void* p) {
+// memory, or page-locked host memory (read over the CPU-GPU link; *host is set);
+// NULL for pageable memory, which must be copied.
+const void* device_view(const void* p, bool* host = nullptr) {
     cudaPointerAttributes at{};
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
+    if (host) *host = at.type == cudaMemoryTypeHost;
     if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged || at.type == cudaMemoryTypeHost)
         return at.devicePointer;
     return nullptr;
@@ -1141,13 +1148,13 @@ int submit_impl(rtc_loop* L, const rtc_chunk* c) {
     // row a later chunk's subaperture row would need.  Otherwise copy it into
     // the loop's frame buffer.
     FramePtrs fp = internal_frames(L);
-    bool in_place = false;
+    bool in_place = false, host_px = false;
     if (w.kind == RTC_WFS_SH && (c->pitch & 15u) == 0 && (reinterpret_cast<uintptr_t>(c->px) & 15u) == 0 &&
         c->pitch >= round_up((size_t)w.width * 2, 16)) {
         const bool needed_here = upto == done || w.oy + done * w.npx >= c->row_begin;
         const bool no_leftover = upto >= w.nsuby || c->row_end <= w.oy + upto * w.npx;
         if (needed_here && no_leftover) {
-            if (const void* dv = device_view(c->px)) {
+            if (const void* dv = device_view(c->px, &host_px)) {
                 in_place = true;
                 fp.px[k] = static_cast<const uint16_t*>(dv);
                 fp.pitch[k] = (long long)(c->pitch / 2);
@@ -1161,7 +1168,7 @@ int submit_impl(rtc_loop* L, const rtc_chunk* c) {
     L->rows_in[k] = c->row_end;
     const bool slopes_launched = upto > done;
     if (slopes_launched) {
-        TRY(slopes_rows(L, r0 + done, r0 + upto, fp, sk));
+        TRY(slopes_rows(L, r0 + done, r0 + upto, fp, in_place && host_px, sk));
         L->rows_done[k] = upto;
     }
     if (last && L->stage_timing) CK(L, cudaEventRecord(s.ev_slopes, sk));
@@ -1194,7 +1201,10 @@ int enqueue_whole_frame(rtc_loop* L, const FramePtrs& fp) {
         TRY(record(L, s.ev_start, L->st));
         TRY(record(L, s.ev_tail, L->st));
     }
-    TRY(slopes_rows(L, 0, L->nrows, fp, L->st));
+    // Whole frames take the register-light slope kernel even from page-locked host
+    // memory: their hundreds of CTAs need several per SM, and the link's bandwidth,
+    // not its latency, bounds them.
+    TRY(slopes_rows(L, 0, L->nrows, fp, false, L->st));
     if (L->stage_timing) TRY(record(L, s.ev_slopes, L->st));
     const FinaliseArgs fa = fin_args(L);
     CK(L, launch_gemv(L->m_dtype, L->d_M, L->d_blocks, 0, L->nblk, L->na, L->d_s, nullptr, L->d_part, L->na, &fa,

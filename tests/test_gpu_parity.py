@@ -348,6 +348,47 @@ def test_process_frame_from_page_locked_host_memory(rtc, torch_cuda):
             assert np.array_equal(ca, cb)
 
 
+def test_host_pixel_slope_variant_equals_device_frames_bitwise(rtc, torch_cuda):
+    # Row chunks read in place from page-locked host memory take the slope kernel
+    # that keeps all of a thread's pixel rows in flight; whole frames take the other
+    # one.  Strips 48 and 24 subapertures wide give 12 and 3 pixel rows per thread;
+    # the additions keep their order, so chunks, page-locked whole frames and
+    # device-resident frames give the same slopes and commands, bit for bit.
+    torch = torch_cuda
+    rng = np.random.default_rng(97)
+    wa = synth.sh_wfs(rng, 48, 12, 600, 590, 0.2, nblocks=4)
+    wb = synth.sh_wfs(rng, 24, 10, 260, 250, 0.0, nblocks=2)
+    ns = 2 * (synth.num_valid(wa) + synth.num_valid(wb))
+    na = 97
+    cfg = dict(name="host_rows", na=na, ns=ns, wfs=[wa, wb], M=synth.control_matrix(rng, na, ns, sd=1e-2),
+               M_scale=None, M_dtype="f32", P=synth.polc_matrix(rng, na), P_scale=None, P_dtype="f32", gain=0.4,
+               leak=0.02, clip=None, a0=None, ref_slopes=rng.normal(0, 0.05, ns).astype(np.float32))
+    frames = synth.draw_frames(cfg, 3, seed=98)
+
+    def pinned(x):
+        h, w = x.shape
+        t = torch.zeros((h, (w + 7) // 8 * 8), dtype=torch.int16, pin_memory=True)
+        t.numpy()[:, :w] = x.view(np.int16)
+        return t[:, :w]
+
+    plans = [synth.chunk_plan(w, 6) for w in cfg["wfs"]]
+    ora = OracleLoop(cfg)
+    with rtc.Loop(cfg, telemetry=True) as a, rtc.Loop(cfg, telemetry=True) as b, \
+            rtc.Loop(cfg, telemetry=True) as c:
+        for k, f in enumerate(frames):
+            host = [pinned(x) for x in f]
+            a.submit_frame(k + 1, host, plans)          # row chunks, in place over the link
+            b.process_frame(k + 1, host)                # whole frame, in place over the link
+            c.process_frame(k + 1, device_frames(f))    # whole frame in HBM
+            got = [lp.get_commands(timeout_us=WAIT_US) for lp in (a, b, c)]
+            assert [g[0] for g in got] == [k + 1] * 3
+            assert np.array_equal(got[0][1], got[2][1]) and np.array_equal(got[1][1], got[2][1])
+            slopes = [lp.get_telemetry(k + 1, timeout_us=WAIT_US)[0] for lp in (a, b, c)]
+            assert np.array_equal(slopes[0], slopes[2]) and np.array_equal(slopes[1], slopes[2])
+            s_ref, a_ref = ora.step(f)
+            assert rel(slopes[2], s_ref) <= TOL_F32 and rel(got[2][1], a_ref) <= TOL_F32
+
+
 @pytest.mark.parametrize("mode", ["device", "chunked"])
 def test_overlapped_and_serialised_launches_give_identical_commands(rtc, torch_cuda, mode):
     # Without stage timing the MVM (and the POLC product) start before their

@@ -23,7 +23,10 @@ BUDGET = {
     "_ZN3rtc16gemv_kernel_1rowILi0ELi4ELi1EEEvNS_8GemvArgsE": ("float32 MVM, 1 row per warp", 32, 32),
     "_ZN3rtc11gemv_kernelILi1ELi2ELi4ELi4EEEvNS_8GemvArgsE": ("BF16 MVM", 64, 0),
     "_ZN3rtc11gemv_kernelILi2ELi1ELi4ELi4EEEvNS_8GemvArgsE": ("E4M3 MVM", 48, 0),
-    "_ZN3rtc13slopes_kernelENS_9SlopeArgsE": ("slope kernel", 64, 0),
+    "_ZN3rtc13slopes_kernelILb0EEEvNS_9SlopeArgsE": ("slope kernel", 64, 0),
+    # pixels read over the CPU-GPU link: every pixel row of a thread in flight at once (launched for
+    # row chunks and page-locked frames, where a few CTAs per SM are enough)
+    "_ZN3rtc13slopes_kernelILb1EEEvNS_9SlopeArgsE": ("slope kernel, host pixels", 168, 0),
 }
 
 
