@@ -943,7 +943,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--paced-frames", type=int, default=10000, help="camera-paced frames per matrix format")
+    ap.add_argument("--paced-frames", type=int, default=20000, help="camera-paced frames per matrix format")
     ap.add_argument("--paced-warmup", type=int, default=500)
     ap.add_argument("--parity-frames", type=int, default=20, help="frames checked against the FP64 oracle")
     ap.add_argument("--swap-frames", type=int, default=2500, help="paced frames of the parameter-swap run")

@@ -1,6 +1,12 @@
 """Edge cases of the CUDA path against the FP64 oracle, through the C ABI: the
 largest WFS count, sensors with no valid unit, one column block per slope row,
-a single actuator, frame ids at the top of their range."""
+a single actuator, frame ids at the top of their range, slope threads with more
+pixel rows than the host-pixel kernel keeps in flight."""
+import os
+import subprocess
+import sys
+import textwrap
+
 import numpy as np
 import pytest
 
@@ -161,3 +167,54 @@ def test_server_release_while_another_thread_submits(rtc, torch_cuda):
         th.join(timeout=30)
         assert not th.is_alive() and not errors and count[0] > 0
         assert srv.usage()["used"] == 0
+
+
+ROWS_BEYOND_SCRIPT = textwrap.dedent("""
+    import numpy as np, torch
+    from oracle import OracleLoop
+    from paper_1903_01852_gb300 import binding as rtc, synth
+    rng = np.random.default_rng(211)
+    w = synth.sh_wfs(rng, 24, 24, 600, 590, 0.0, nblocks=3)
+    ns = 2 * synth.num_valid(w)
+    na = 41
+    cfg = dict(name="rows_beyond", na=na, ns=ns, wfs=[w], M=synth.control_matrix(rng, na, ns, sd=1e-2),
+               M_scale=None, M_dtype="f32", P=synth.polc_matrix(rng, na), P_scale=None, P_dtype="f32", gain=0.4,
+               leak=0.02, clip=None, a0=None, ref_slopes=rng.normal(0, 0.05, ns).astype(np.float32))
+    frames = synth.draw_frames(cfg, 3, seed=212)
+    plans = [synth.chunk_plan(w, 4)]
+    ora = OracleLoop(cfg)
+    worst = 0.0
+    with rtc.Loop(cfg, telemetry=True) as a, rtc.Loop(cfg, telemetry=True) as c:
+        for k, f in enumerate(frames):
+            x = f[0]
+            h, wd = x.shape
+            t = torch.zeros((h, (wd + 7) // 8 * 8), dtype=torch.int16, pin_memory=True)
+            t.numpy()[:, :wd] = x.view(np.int16)
+            d = torch.zeros((h, (wd + 7) // 8 * 8), dtype=torch.int16, device="cuda")
+            d[:, :wd] = torch.from_numpy(x.view(np.int16)).cuda()
+            a.submit_frame(k + 1, [t[:, :wd]], plans)
+            c.process_frame(k + 1, [d[:, :wd]])
+            (fa, ca), (fc, cc) = a.get_commands(timeout_us=30_000_000), c.get_commands(timeout_us=30_000_000)
+            sa, sc = a.get_telemetry(fa, timeout_us=30_000_000)[0], c.get_telemetry(fc, timeout_us=30_000_000)[0]
+            assert fa == fc == k + 1 and np.array_equal(ca, cc) and np.array_equal(sa, sc)
+            s_ref, a_ref = ora.step(f)
+            rel = lambda u, v: float(np.max(np.abs(u - v)) / max(np.max(np.abs(v)), 1e-30))
+            worst = max(worst, rel(sc, s_ref), rel(cc, a_ref))
+    assert worst <= 1e-5, worst
+    print("ok", worst)
+""")
+
+
+def test_host_pixel_rows_beyond_the_in_flight_window(torch_cuda, tmp_path):
+    # The host-pixel slope kernel keeps at most 12 pixel rows of a thread in flight
+    # and the default part split never gives a thread more; a build allowing 30
+    # rows per thread runs the rest of that path: 24-pixel subapertures read in
+    # place from page-locked row chunks (24 rows per thread) against device frames.
+    from paper_1903_01852_gb300.build import build
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    lib = build(defines=["RTC_SLOPE_ROWS_PER_THREAD=30"], out=str(tmp_path / "librtc.so"))
+    env = dict(os.environ, RTC_LIBRARY=lib, PYTHONPATH=root + os.pathsep + os.environ.get("PYTHONPATH", ""))
+    r = subprocess.run([sys.executable, "-c", ROWS_BEYOND_SCRIPT], env=env, capture_output=True, text=True,
+                       timeout=600, cwd=root)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-3000:]
+    assert r.stdout.startswith("ok")
