@@ -13,6 +13,7 @@
 //   telemetry_kernel one entry of the telemetry circular buffer (Section 3.3)
 //   pack / relayout / quantize / check kernels used at creation and for telemetry
 #include <algorithm>
+#include <type_traits>
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -494,25 +495,50 @@ __device__ __forceinline__ uint4 ld_stream(const uint4* p) {
 __device__ __forceinline__ float bf_lo(uint32_t u) { return __uint_as_float(u << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
 
-__device__ __forceinline__ float dot_f32(const uint4& m, const float4* x, float acc) {
+#ifndef RTC_GEMV_FFMA2_MASK
+#define RTC_GEMV_FFMA2_MASK 1      // storage formats (bit 1 << dtype) that sum with packed FMAs: float32
+#endif
+// A lane's running sum: one float32 FMA per element in element order (float), or
+// two float32 partial sums over the even and odd elements advanced with the packed
+// fma.rn.f32x2 (half the FMA instructions).
+using acc_pk = unsigned long long;
+__device__ __forceinline__ void acc_zero(float& c) { c = 0.f; }
+__device__ __forceinline__ void acc_zero(acc_pk& c) { c = 0ull; }
+__device__ __forceinline__ float fma2(float a0, float a1, float b0, float b1, float c) {
+    return fmaf(a1, b1, fmaf(a0, b0, c));
+}
+__device__ __forceinline__ acc_pk fma2(float a0, float a1, float b0, float b1, acc_pk c) {
+    acc_pk a, b, d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(a) : "f"(a0), "f"(a1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(b) : "f"(b0), "f"(b1));
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ float acc_total(float c) { return c; }
+__device__ __forceinline__ float acc_total(acc_pk c) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(c));
+    return lo + hi;
+}
+template <int DT> struct AccOf {
+    using type = typename std::conditional<((RTC_GEMV_FFMA2_MASK >> DT) & 1) != 0, acc_pk, float>::type;
+};
+
+template <typename A>
+__device__ __forceinline__ A dot_f32(const uint4& m, const float4* x, A acc) {
     const float4 xv = __ldg(x);
-    acc = fmaf(__uint_as_float(m.x), xv.x, acc);
-    acc = fmaf(__uint_as_float(m.y), xv.y, acc);
-    acc = fmaf(__uint_as_float(m.z), xv.z, acc);
-    acc = fmaf(__uint_as_float(m.w), xv.w, acc);
+    acc = fma2(__uint_as_float(m.x), __uint_as_float(m.y), xv.x, xv.y, acc);
+    acc = fma2(__uint_as_float(m.z), __uint_as_float(m.w), xv.z, xv.w, acc);
     return acc;
 }
 
-__device__ __forceinline__ float dot_bf16(const uint4& m, const float4* x, float acc) {
+template <typename A>
+__device__ __forceinline__ A dot_bf16(const uint4& m, const float4* x, A acc) {
     const float4 a = __ldg(x), b = __ldg(x + 1);
-    acc = fmaf(bf_lo(m.x), a.x, acc);
-    acc = fmaf(bf_hi(m.x), a.y, acc);
-    acc = fmaf(bf_lo(m.y), a.z, acc);
-    acc = fmaf(bf_hi(m.y), a.w, acc);
-    acc = fmaf(bf_lo(m.z), b.x, acc);
-    acc = fmaf(bf_hi(m.z), b.y, acc);
-    acc = fmaf(bf_lo(m.w), b.z, acc);
-    acc = fmaf(bf_hi(m.w), b.w, acc);
+    acc = fma2(bf_lo(m.x), bf_hi(m.x), a.x, a.y, acc);
+    acc = fma2(bf_lo(m.y), bf_hi(m.y), a.z, a.w, acc);
+    acc = fma2(bf_lo(m.z), bf_hi(m.z), b.x, b.y, acc);
+    acc = fma2(bf_lo(m.w), bf_hi(m.w), b.z, b.w, acc);
     return acc;
 }
 
@@ -521,23 +547,22 @@ __device__ __forceinline__ float2 e4m3x2(uint32_t pair16) {
     return __half22float2(*reinterpret_cast<const __half2*>(&h));
 }
 
-__device__ __forceinline__ float dot_e4m3(const uint4& m, const float4* x, float acc) {
+template <typename A>
+__device__ __forceinline__ A dot_e4m3(const uint4& m, const float4* x, A acc) {
     const uint32_t w[4] = {m.x, m.y, m.z, m.w};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const float4 xv = __ldg(x + k);
         const float2 lo = e4m3x2(w[k] & 0xffffu);
         const float2 hi = e4m3x2(w[k] >> 16);
-        acc = fmaf(lo.x, xv.x, acc);
-        acc = fmaf(lo.y, xv.y, acc);
-        acc = fmaf(hi.x, xv.z, acc);
-        acc = fmaf(hi.y, xv.w, acc);
+        acc = fma2(lo.x, lo.y, xv.x, xv.y, acc);
+        acc = fma2(hi.x, hi.y, xv.z, xv.w, acc);
     }
     return acc;
 }
 
-template <int DT>
-__device__ __forceinline__ float dot16(const uint4& m, const float* x, int v, float acc) {
+template <int DT, typename A>
+__device__ __forceinline__ A dot16(const uint4& m, const float* x, int v, A acc) {
     const float4* xp = reinterpret_cast<const float4*>(x) + v * (Elem<DT>::kPer16 / 4);
     if constexpr (DT == RTC_F32) return dot_f32(m, xp, acc);
     else if constexpr (DT == RTC_BF16) return dot_bf16(m, xp, acc);
@@ -650,13 +675,13 @@ __device__ __forceinline__ void gemv_body(const GemvArgs& a) {
     for (int rr = 0; rr < RPW; rr += RI) {
         const uint4* mrow[RI];
         bool ok[RI];
-        float acc[RI];
+        typename AccOf<DT>::type acc[RI];
 #pragma unroll
         for (int i = 0; i < RI; ++i) {
             const int r = rbase + rr + i;
             ok[i] = r < a.na;
             mrow[i] = reinterpret_cast<const uint4*>(a.M + (size_t)(B.m_off + (long long)(ok[i] ? r : 0) * B.pitch) * esz);
-            acc[i] = 0.f;
+            acc_zero(acc[i]);
         }
 #pragma unroll 1
         for (int v0 = lane; v0 < nvec; v0 += 32 * U) {
@@ -679,7 +704,7 @@ __device__ __forceinline__ void gemv_body(const GemvArgs& a) {
         }
 #pragma unroll
         for (int i = 0; i < RI; ++i) {
-            const float t = warp_sum(acc[i]);
+            const float t = warp_sum(acc_total(acc[i]));
             const int r = rbase + rr + i;
             if (lane == 0 && ok[i]) a.out[(long long)b * a.out_stride + r] = a.out_scale ? t * a.out_scale[r] : t;
         }
@@ -832,6 +857,10 @@ cudaError_t launch_gemv_t(const GemvArgs& base, int nb, long long avg_row_bytes,
     while (rpw > RI &&
            (long long)((na + kGemvWarps * rpw - 1) / (kGemvWarps * rpw)) * nb < RTC_GEMV_MIN_WAVES * 8LL * 152)
         rpw /= 2;
+    // with packed sums two rows per warp take 34 registers (6 CTAs per SM): such
+    // launches run one row per warp instead (same sums, at most 32 registers)
+    constexpr bool kNoRpw2 = RI == 1 && std::is_same<typename AccOf<DT>::type, acc_pk>::value;
+    if (kNoRpw2 && rpw == 2) rpw = 1;
     GemvArgs a = base;
     a.tiles = (na + kGemvWarps * rpw - 1) / (kGemvWarps * rpw);
     const dim3 grid((unsigned)(a.tiles * nb));
@@ -839,7 +868,8 @@ cudaError_t launch_gemv_t(const GemvArgs& base, int nb, long long avg_row_bytes,
     const long long tile_bytes = std::max(1LL, avg_row_bytes * kGemvWarps * rpw);
     a.prefetch_ctas = pdl ? (int)std::min<long long>(grid.x, (96LL << 20) / tile_bytes) : 0;
     if (rpw >= 4) return launch_maybe_pdl(gemv_kernel<DT, U, RI, (RI > 4 ? RI : 4)>, grid, a, pdl, st);
-    if (rpw >= 2) return launch_maybe_pdl(gemv_kernel<DT, U, RI, (RI > 2 ? RI : 2)>, grid, a, pdl, st);
+    if constexpr (!kNoRpw2)
+        if (rpw >= 2) return launch_maybe_pdl(gemv_kernel<DT, U, RI, (RI > 2 ? RI : 2)>, grid, a, pdl, st);
     if constexpr (RI == 1) return launch_maybe_pdl(gemv_kernel_1row<DT, U, 1>, grid, a, pdl, st);
     else return launch_maybe_pdl(gemv_kernel<DT, U, RI, RI>, grid, a, pdl, st);
 }
