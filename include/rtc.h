@@ -77,7 +77,8 @@ extern "C" {
 #define RTC_FLAG_STAGE_TIMING 4u /* also time the slope and MVM kernels separately; this
                                     serialises them (no early start of the MVM) */
 #define RTC_FLAG_UPDATABLE  8u /* keep shadow copies of the parameters for rtc_update
-                                  (twice the matrix memory) */
+                                  (twice the matrix memory, plus 64 MiB of page-locked
+                                  host memory to stage the uploads) */
 #define RTC_FLAG_GRAPHS    16u /* page-locked input frames per ring slot and one captured CUDA
                                   graph per slot (rtc_next_frame_buffers, rtc_submit_frame_graph);
                                   excludes RTC_FLAG_UPDATABLE and RTC_FLAG_STAGE_TIMING */
@@ -379,7 +380,9 @@ typedef struct rtc_update_desc {
  * low-priority stream while frames keep running, then the first frame that
  * starts after this call returns uses them (the swap is a host-side pointer
  * exchange at the frame boundary, with no work added to that frame on the
- * GPU).  The POLC term that frame uses was computed with the previous P; the
+ * GPU).  The matrices are gathered by the calling thread into two page-locked
+ * staging buffers and copied from there, so no driver call holds a large
+ * pageable copy.  The POLC term that frame uses was computed with the previous P; the
  * new P applies from that frame's own POLC product on.  Blocks the calling
  * thread (not the submitting one) until the upload is done; a second call
  * before the swap replaces the pending values.  Needs RTC_FLAG_UPDATABLE;

@@ -146,6 +146,11 @@ struct rtc_loop {
     std::vector<WfsDev> wfs_host;           // the active WFS table as last uploaded
     cudaStream_t st_up = nullptr;
     cudaEvent_t ev_swap = nullptr;
+    // two page-locked staging buffers for the large uploads of rtc_update
+    unsigned char* h_stage[2] = {nullptr, nullptr};
+    cudaEvent_t ev_stage[2] = {nullptr, nullptr};
+    bool stage_used[2] = {false, false};
+    int stage_next = 0;
     bool swap_ev_valid = false;
     std::mutex upd_mu;                      // held by rtc_update; the submitting thread only try-locks it
     bool upd_pending = false;
@@ -227,6 +232,7 @@ bool all_finite(const float* p, size_t n) {
 // Every allocation carries kGuardBytes of kGuardByte after its end; rtc_check_guards
 // reports any that a kernel (or a copy) overwrote.
 constexpr size_t kGuardBytes = 256;
+constexpr size_t kStageBytes = size_t(32) << 20;   // each of the two upload staging buffers
 constexpr unsigned char kGuardByte = 0xA5;
 
 template <typename T>
@@ -310,6 +316,10 @@ void release(rtc_loop* L) {
     if (L->h_tel) cudaFreeHost(L->h_tel);
     if (L->st_up) cudaStreamSynchronize(L->st_up);
     if (L->ev_swap) cudaEventDestroy(L->ev_swap);
+    for (int b = 0; b < 2; ++b) {
+        if (L->ev_stage[b]) cudaEventDestroy(L->ev_stage[b]);
+        if (L->h_stage[b]) cudaFreeHost(L->h_stage[b]);
+    }
     if (L->st) cudaStreamDestroy(L->st);
     if (L->st_tel) cudaStreamDestroy(L->st_tel);
     if (L->st_up) cudaStreamDestroy(L->st_up);
@@ -743,6 +753,14 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
         TRY(dev_alloc(L, &L->sh_wfs, wdev.size() * sizeof(WfsDev)));
         CK(L, cudaStreamCreateWithPriority(&L->st_up, cudaStreamNonBlocking, 0));
         CK(L, cudaEventCreateWithFlags(&L->ev_swap, cudaEventDisableTiming));
+        for (int b = 0; b < 2; ++b) {
+            void* dv = nullptr;
+            void* hv = nullptr;
+            const int rc = pinned_alloc(L, &hv, &dv, kStageBytes, "upload staging buffer");
+            L->h_stage[b] = static_cast<unsigned char*>(hv);
+            TRY(rc);
+            CK(L, cudaEventCreateWithFlags(&L->ev_stage[b], cudaEventDisableTiming));
+        }
         L->upd_dark.assign(L->nwfs, 0);
         L->upd_flat.assign(L->nwfs, 0);
     }
@@ -1292,6 +1310,39 @@ int process_impl(rtc_loop* L, uint64_t id, const uint16_t* const* px, const size
     return status;
 }
 
+// Upload rows x width bytes from pageable host memory (row pitch spitch) into
+// device memory (row pitch dpitch >= width, the bytes past width written as
+// zeros) on the upload stream, through the loop's two page-locked staging
+// buffers: this thread gathers one piece while the copy engine moves the
+// previous one, and every CUDA call is a short asynchronous copy from page-locked
+// memory (a pageable copy of a large matrix would be staged inside the driver,
+// where it has delayed the frame thread's launches).  Rows wider than a staging
+// buffer fall back to one pitched pageable copy.
+int staged_upload(rtc_loop* L, void* dst, size_t dpitch, const void* src, size_t spitch, size_t width, size_t rows) {
+    if (dpitch > kStageBytes) {
+        CK(L, cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, rows, cudaMemcpyHostToDevice, L->st_up));
+        return RTC_OK;
+    }
+    const size_t per = kStageBytes / dpitch;
+    for (size_t r0 = 0; r0 < rows; r0 += per) {
+        const size_t n = std::min(per, rows - r0);
+        const int b = L->stage_next;
+        L->stage_next ^= 1;
+        if (L->stage_used[b]) CK(L, cudaEventSynchronize(L->ev_stage[b]));   // its previous copy is done
+        unsigned char* h = L->h_stage[b];
+        const unsigned char* from = static_cast<const unsigned char*>(src) + r0 * spitch;
+        for (size_t r = 0; r < n; ++r) {
+            std::memcpy(h + r * dpitch, from + r * spitch, width);
+            if (dpitch > width) std::memset(h + r * dpitch + width, 0, dpitch - width);
+        }
+        CK(L, cudaMemcpyAsync(static_cast<unsigned char*>(dst) + r0 * dpitch, h, n * dpitch, cudaMemcpyHostToDevice,
+                              L->st_up));
+        CK(L, cudaEventRecord(L->ev_stage[b], L->st_up));
+        L->stage_used[b] = true;
+    }
+    return RTC_OK;
+}
+
 // Busy-poll an event until done or the deadline.
 int wait_event(rtc_loop* L, cudaEvent_t ev, Clock::time_point deadline, bool forever) {
     for (;;) {
@@ -1676,9 +1727,9 @@ int rtc_update(rtc_loop* L, const rtc_update_desc* d) {
     if (d->M) {
         for (const BlockDev& B : L->blocks_h)
             if (B.ncols)
-                CK(L, cudaMemcpy2DAsync(static_cast<uint8_t*>(L->sh_M) + (size_t)B.m_off * esz, (size_t)B.pitch * esz,
-                                        static_cast<const uint8_t*>(d->M) + (size_t)B.c0 * esz, (size_t)L->ns * esz,
-                                        (size_t)B.ncols * esz, L->na, cudaMemcpyHostToDevice, L->st_up));
+                TRY(staged_upload(L, static_cast<uint8_t*>(L->sh_M) + (size_t)B.m_off * esz, (size_t)B.pitch * esz,
+                                  static_cast<const uint8_t*>(d->M) + (size_t)B.c0 * esz, (size_t)L->ns * esz,
+                                  (size_t)B.ncols * esz, L->na));
         mask |= kUpdM;
     }
     if (d->M_scale) {
@@ -1688,8 +1739,7 @@ int rtc_update(rtc_loop* L, const rtc_update_desc* d) {
     if (d->P) {
         const size_t pe = dtype_size(L->p_dtype);
         const size_t pitch = round_up((size_t)L->na, elems_per_16B(L->p_dtype));
-        CK(L, cudaMemcpy2DAsync(L->sh_P, pitch * pe, d->P, (size_t)L->na * pe, (size_t)L->na * pe, L->na,
-                                cudaMemcpyHostToDevice, L->st_up));
+        TRY(staged_upload(L, L->sh_P, pitch * pe, d->P, (size_t)L->na * pe, (size_t)L->na * pe, L->na));
         mask |= kUpdP;
     }
     if (d->P_scale) {
@@ -1732,6 +1782,7 @@ int rtc_update(rtc_loop* L, const rtc_update_desc* d) {
         mask |= kUpdTable;
     }
     CK(L, cudaStreamSynchronize(L->st_up));
+    L->stage_used[0] = L->stage_used[1] = false;
     if (d->set_control) {
         L->upd_ctrl = true;
         L->upd_gain = d->gain;

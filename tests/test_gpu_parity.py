@@ -452,6 +452,33 @@ def test_parameter_swap_takes_effect_at_the_next_frame(rtc, torch_cuda):
         assert loop.info()["swaps"] == 1
 
 
+@pytest.mark.parametrize("fmt", ["bf16", "e4m3"])
+def test_parameter_swap_with_quantised_matrices(rtc, torch_cuda, fmt):
+    # 2- and 1-byte codes go through the same staged upload as float32 matrices
+    # (rows gathered into page-locked staging buffers, padding written as zeros).
+    from oracle import stored_matrix
+    cfg = ragged_config(seed=131)
+    new = ragged_config(seed=132)
+    for c in (cfg, new):
+        codes, scale = quantize_rows(c["M"], fmt)
+        pc, ps = quantize_rows(c["P"], fmt)
+        c.update(M=codes, M_scale=scale, M_dtype=fmt, P=pc, P_scale=ps, P_dtype=fmt)
+    frames = synth.draw_frames(cfg, 6, seed=133)
+    ref = OracleLoop(cfg)
+    with rtc.Loop(cfg, telemetry=True, updatable=True) as loop:
+        for k in range(2):
+            loop.submit_frame(k + 1, frames[k])
+            assert rel(loop.get_commands(timeout_us=WAIT_US)[1], ref.step(frames[k])[1]) <= TOL_F32
+        loop.update(M=new["M"], M_scale=new["M_scale"], P=new["P"], P_scale=new["P_scale"])
+        ref.m = stored_matrix(new["M"], fmt, new["M_scale"])
+        ref.p = stored_matrix(new["P"], fmt, new["P_scale"])
+        for k in range(2, 6):
+            loop.submit_frame(k + 1, frames[k])
+            a = loop.get_commands(timeout_us=WAIT_US)[1]
+            assert rel(a, ref.step(frames[k])[1]) <= TOL_F32, k
+        assert loop.info()["swaps"] == 1
+
+
 def test_update_while_frames_run_and_rejected_updates(rtc, torch_cuda):
     import threading
     cfg = synth.make_config("elt_scao_sh", polc=True)
