@@ -181,7 +181,7 @@ __device__ void sh_part(const SlopePart& P, const SlopeRow& row, const WfsDev& W
                     }
                 }
             }
-            r += kRowsInFlight * G;    // rows beyond (never with the create-time part split) go below
+            r += kRowsInFlight * G;    // rows beyond (never with the default part split) go below
         }
         for (; r + 3 * G < P.pr1; r += 4 * G) {
             uint2 rw[4];
