@@ -1,7 +1,8 @@
 """Seeded random configurations against the FP64 oracle, through the C ABI:
 geometry (SH and pyramid sizes, origins, valid masks, block counts), frame
 sizes, chunk plans, thresholds and modes, reference slopes, POLC form, clip and
-matrix storage are all drawn per case."""
+matrix storage are all drawn per case.  Half of the chunked cases submit their
+chunks from page-locked host memory, which the slope kernel reads in place."""
 import numpy as np
 import pytest
 
@@ -77,6 +78,17 @@ def random_case(seed):
     return cfg, mode, nchunks, rng
 
 
+def pinned_frames(frames, torch):
+    """Page-locked copies with a 16-byte row pitch, so whole-subaperture-row chunks are read in place."""
+    out = []
+    for x in frames:
+        h, w = x.shape
+        t = torch.zeros((h, (w + 7) // 8 * 8), dtype=torch.int16, pin_memory=True)
+        t.numpy()[:, :w] = x.view(np.int16)
+        out.append(t[:, :w])
+    return out
+
+
 @pytest.mark.parametrize("seed", range(CASES))
 def test_random_configuration(rtc, torch_cuda, seed):
     cfg, mode, nchunks, rng = random_case(7000 + seed)
@@ -92,7 +104,8 @@ def test_random_configuration(rtc, torch_cuda, seed):
             elif mode == "rows":
                 loop.submit_frame(fid, f, [[(r, r + 1) for r in range(x.shape[0])] for x in f])
             else:
-                loop.submit_frame(fid, f, [synth.chunk_plan(w, nchunks) for w in cfg["wfs"]])
+                loop.submit_frame(fid, pinned_frames(f, torch_cuda) if seed % 2 == 0 else f,
+                                  [synth.chunk_plan(w, nchunks) for w in cfg["wfs"]])
             got, a = loop.get_commands(timeout_us=WAIT_US)
             s, _ = loop.get_telemetry(fid, timeout_us=WAIT_US)
             s_ref, a_ref = ref.step(f)
