@@ -203,7 +203,9 @@ typedef struct rtc_polc {
 
 typedef struct rtc_loop rtc_loop;   /* opaque */
 
-/* Validate the description, copy every map and matrix into device memory of
+/* A control loop (Fig. ao_diag: pixel handling, reconstruction, control law;
+ * Table ao_compare: the instrument configurations).  Validate the
+ * description, copy every map and matrix into device memory of
  * geometry->device (admission fails with RTC_ENOMEM when they do not fit),
  * build the slope-row and column-block plans, allocate the page-locked
  * command ring and the CUDA streams and events.  On success *out is a new
@@ -247,12 +249,14 @@ typedef struct rtc_chunk {
  * has returned this frame. */
 int rtc_submit_pixels(rtc_loop* loop, const rtc_chunk* chunk);
 
-/* Whole-frame entry point for frames already resident in device memory
- * (e.g. written there by a frame grabber): px[w] is a device pointer to WFS
- * w's frame (16-byte aligned), pitch[w] its row pitch in bytes (a multiple
- * of 16, >= 2*width rounded up to 16).  The slope kernels read the frames in
- * place; they must stay unchanged until rtc_get_commands returns this frame.
- * Otherwise behaves like submitting every row of every WFS at once. */
+/* Whole-frame entry point (Section 2.2's pixel handling for a whole frame at
+ * once), for frames in device memory (e.g. written there by a frame grabber)
+ * or in page-locked host memory (read over the CPU-GPU link): px[w] points at
+ * WFS w's frame (16-byte aligned), pitch[w] is its row pitch in bytes (a
+ * multiple of 16, >= 2*width rounded up to 16); pageable memory is rejected
+ * with RTC_EINVAL.  The slope kernels read the frames in place; they must
+ * stay unchanged until rtc_get_commands returns this frame.  Otherwise
+ * behaves like submitting every row of every WFS at once. */
 int rtc_process_frame(rtc_loop* loop, uint64_t frame_id,
                       const uint16_t* const* px, const size_t* pitch);
 
@@ -269,8 +273,10 @@ int rtc_next_frame_buffers(rtc_loop* loop, uint16_t** px, size_t* pitch);
  * rules as rtc_process_frame. */
 int rtc_submit_frame_graph(rtc_loop* loop, uint64_t frame_id);
 
-/* Wait (busy-polling, up to timeout_us microseconds; <0 waits forever) for
- * the oldest frame whose pixels are all submitted and whose commands have not
+/* The DM commands of a frame (Section 3: the master's sum of the partial
+ * commands after POLC and the control law, tagged with the camera frame
+ * number).  Wait (busy-polling, up to timeout_us microseconds; <0 waits
+ * forever) for the oldest frame whose pixels are all submitted and whose commands have not
  * yet been returned, then copy its na commands to out (host) and its frame
  * id to *frame_id.  RTC_ETIMEDOUT leaves that frame queued.  The ring keeps
  * the last `ring` frames; older unread ones are discarded. */
@@ -284,8 +290,8 @@ int rtc_get_commands(rtc_loop* loop, float* out, size_t n, uint64_t* frame_id,
 int rtc_get_telemetry(rtc_loop* loop, uint64_t frame_id, float* slopes, size_t ns,
                       float* cmds, size_t na, int64_t timeout_us);
 
-/* Device times of one frame, from CUDA events on the loop's stream (needs
- * RTC_FLAG_TIMING).  latency_us: for rtc_process_frame, from just before the
+/* Device times of one frame (the latency of Table ao_results, measured on the
+ * GPU), from CUDA events on the loop's stream (needs RTC_FLAG_TIMING).  latency_us: for rtc_process_frame, from just before the
  * slope kernel to the end of the MVM kernel, whose tail writes the commands;
  * for chunked frames, from just before the last chunk's work.  frame_us: from
  * the frame's first submitted work to the commands.  polc_us: the POLC
@@ -391,7 +397,9 @@ int rtc_update(rtc_loop* loop, const rtc_update_desc* desc);
 
 /* ---- state and introspection ---------------------------------------- */
 
-/* Wait for queued work, then copy the integrator state a (na floats) out. */
+/* The control-law state (the DM commands a of the last frame, on which the
+ * implicit-POLC term of Section 3.4 acts).  Wait for queued work, then copy
+ * the integrator state a (na floats) out. */
 int rtc_get_state(rtc_loop* loop, float* a, size_t na);
 /* Wait for queued work, then set a and recompute q = P a, or u = D a in
  * explicit-POLC mode (checkpoint resume). */
@@ -421,7 +429,8 @@ typedef struct rtc_info {
 } rtc_info;
 int rtc_get_info(rtc_loop* loop, rtc_info* out);
 
-/* Device memory a loop with this description would hold once created
+/* No counterpart in the paper (DARC sizes nodes by hand): device memory a loop
+ * with this description would hold once created
  * (resident_bytes) and at most during creation (peak_bytes, with the upload
  * buffers), computed from the description alone without touching the GPU;
  * this is what admission by HBM footprint uses.  Validation as rtc_create. */
@@ -434,8 +443,10 @@ const char* rtc_last_error(const rtc_loop* loop);
 
 /* ---- stateless device operations ------------------------------------ */
 
-/* Per-row scaled quantisation of a float32 matrix in device memory, for
- * storing M or P in BF16 or E4M3 (halving / quartering the bytes the MVM
+/* Per-row scaled quantisation of a float32 matrix in device memory (no
+ * counterpart in the paper, whose matrices are float32: reduced-precision
+ * storage for the memory-bound MVM of Section 2.3), for storing M or P in BF16
+ * or E4M3 (halving / quartering the bytes the MVM
  * streams).  scale_r = max_j |M_rj| (BF16) or max_j |M_rj| / 448 (E4M3),
  * 1 for an all-zero row; code_rj = round-to-nearest-even of fl(M_rj/scale_r),
  * saturating at +-448 for E4M3.  M: device float32, row r at M + r*ld.
