@@ -525,13 +525,18 @@ const char* rtc_server_last_error(const rtc_server* server);
  * device float32[na] or NULL (1 and 0); a_in, a_out: device float32[na], may
  * be the same buffer.  The partial sums of the column splits go to a static
  * device array of RTC_NOALLOC_MAX_FLOATS floats; na larger than that returns
- * RTC_EINVAL, as do NULL or misaligned pointers.  The first call on each
- * device looks up that array's device address with the device current, so
- * make one call on each device before any stream capture.  Every call shares
- * the array: calls whose work overlaps on the GPU (other streams, other host
- * threads) race on it and must be serialised by the caller.  Nothing in the
- * array needs clearing: every call overwrites the part it reads.  stream: a
- * cudaStream_t or NULL; asynchronous.  Returns RTC_ECUDA if a launch fails. */
+ * RTC_EINVAL, as do NULL or misaligned pointers.  It runs in the context
+ * current on the calling thread: the current device's primary context (the
+ * CUDA runtime's default), or a driver-API context the caller created and made
+ * current.  Each context has its own copy of the array, so the first call in
+ * each context (and again after cudaDeviceReset, which ends the old one) looks
+ * up the array's device address there; make that first call before any stream
+ * capture.  Every call shares the array: calls whose work overlaps on the GPU
+ * (other streams, other host threads) race on it and must be serialised by the
+ * caller.  Nothing in the array needs clearing: every call overwrites the part
+ * it reads.  stream: a cudaStream_t or NULL; asynchronous.  Returns RTC_ECUDA,
+ * without launching and without clearing it, when a CUDA error from the
+ * caller's earlier work is still pending, and RTC_ECUDA if a launch fails. */
 int rtc_reconstruct_noalloc(int32_t na, int32_t ns, const float* M, size_t ld,
                             const float* row_scale, const float* s, const float* q,
                             const float* a_in, float* a_out, float gain, float leak,

@@ -10,6 +10,7 @@
 // would otherwise allocate.
 #include <algorithm>
 #include <mutex>
+#include <utility>
 #include <vector>
 
 #include "rtc_internal.h"
@@ -66,23 +67,70 @@ __global__ void split_finalise_kernel(const float* __restrict__ part, int nsplit
     a_out[r] = fmaf(gain, w, oml * a_in[r]);
 }
 
-// Device address of the scratch array, looked up once per device with that
-// device current (host code cannot use the symbol itself as a device pointer).
+// The scratch array's address belongs to a context: the primary context of a
+// device, a driver-API context the caller made current, or the primary context
+// re-created after cudaDeviceReset each have their own copy of the module.  The
+// address is therefore looked up once per context, keyed by the driver's
+// context id (unique for the life of the process, never reused), with that
+// context current.  The two driver calls are resolved through the runtime, so
+// the library needs no link against the driver library.
+using CtxGetCurrentFn = int (*)(void** ctx);          // CUresult cuCtxGetCurrent(CUcontext*)
+using CtxGetIdFn = int (*)(void* ctx, unsigned long long* id);  // CUresult cuCtxGetId(CUcontext, id*)
+
+struct DriverFns {
+    CtxGetCurrentFn get_current = nullptr;
+    CtxGetIdFn get_id = nullptr;
+};
+
+const DriverFns& driver_fns() {
+    static DriverFns fns;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fns.get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fns.get_id = reinterpret_cast<CtxGetIdFn>(p);
+    });
+    return fns;
+}
+
+// Id of the context current on this thread; 0 if there is none or it cannot be read.
+unsigned long long current_context_id() {
+    const DriverFns& d = driver_fns();
+    if (!d.get_current || !d.get_id) return 0;
+    void* ctx = nullptr;
+    if (d.get_current(&ctx) != 0 || !ctx) return 0;
+    unsigned long long id = 0;
+    return d.get_id(ctx, &id) == 0 ? id : 0;
+}
+
 float* scratch_address(cudaError_t* err) {
     static std::mutex mu;
-    static std::vector<float*> addr;
-    int dev = -1;
-    *err = cudaGetDevice(&dev);
-    if (*err != cudaSuccess) return nullptr;
-    std::lock_guard<std::mutex> g(mu);
-    if ((size_t)dev >= addr.size()) addr.resize(dev + 1, nullptr);
-    if (!addr[dev]) {
+    static std::vector<std::pair<unsigned long long, float*>> addr;   // (context id, address)
+    *err = cudaSuccess;
+    unsigned long long id = current_context_id();
+    if (id == 0) {
+        // No context is current yet: the runtime's lookup below makes the current
+        // device's primary context current; its id is read afterwards.
         void* p = nullptr;
         *err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (*err != cudaSuccess) return nullptr;
-        addr[dev] = static_cast<float*>(p);
+        id = current_context_id();
+        if (id == 0) { *err = cudaErrorDeviceUninitialized; return nullptr; }
     }
-    return addr[dev];
+    std::lock_guard<std::mutex> g(mu);
+    for (const auto& e : addr)
+        if (e.first == id) return e.second;
+    void* p = nullptr;
+    *err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (*err != cudaSuccess) return nullptr;
+    addr.emplace_back(id, static_cast<float*>(p));
+    return static_cast<float*>(p);
 }
 
 }  // namespace
@@ -105,12 +153,16 @@ extern "C" int rtc_reconstruct_noalloc(int32_t na, int32_t ns, const float* M, s
     int split_cols = (ns + nsplit - 1) / nsplit;
     split_cols = (split_cols + 3) / 4 * 4;
     nsplit = (ns + split_cols - 1) / split_cols;
+    // An error left pending by the caller's own earlier work is not ours to
+    // report or to clear: return without launching and leave it in place.
+    if (cudaPeekAtLastError() != cudaSuccess) return RTC_ECUDA;
     cudaError_t e = cudaSuccess;
     float* part = scratch_address(&e);
     if (!part) return RTC_ECUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     split_gemv_kernel<<<dim3((na + kWarps - 1) / kWarps, nsplit), kWarps * 32, 0, st>>>(M, ld, na, ns, split_cols, s,
                                                                                         part);
+    if (cudaGetLastError() != cudaSuccess) return RTC_ECUDA;
     split_finalise_kernel<<<(na + 255) / 256, 256, 0, st>>>(part, nsplit, na, row_scale, q, a_in, a_out, 1.0f - leak,
                                                              gain);
     return cudaGetLastError() == cudaSuccess ? RTC_OK : RTC_ECUDA;

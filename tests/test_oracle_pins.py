@@ -498,3 +498,66 @@ def test_oracle_loop_one_frame_identity_matrix():
     assert np.array_equal(a, 0.5 * s)
     s2, a2 = loop.step([raw])
     assert np.allclose(a2, 0.99 * a + 0.5 * s2, rtol=1e-15, atol=0)
+
+
+def test_two_sensor_frame_slopes_hand_values_in_configuration_order():
+    # An SH sensor (2x2 subapertures of 2x2 px, subaperture (0, 1) invalid) and a
+    # pyramid (2x2 pupil, pixel (1, 0) invalid), slopes worked out by hand: units
+    # row-major within a sensor, x before y, sensors in configuration order, then
+    # the reference slopes subtracted over the concatenation.
+    sh = sh_desc(2, nsub=2, valid=np.array([[1, 0], [1, 1]], np.uint8))
+    sh_raw = np.zeros((4, 4), np.uint16)
+    sh_raw[0, 1], sh_raw[1, 1] = 3, 1               # subap (0,0): F 4, x (3+1)*0.5/4, y (-1.5+0.5)/4
+    sh_raw[0, 3] = 7                                # subap (0,1): invalid, must not appear
+    sh_raw[3, 0] = 2                                # subap (1,0): single pixel at (-0.5, +0.5)
+    sh_raw[2, 2], sh_raw[2, 3], sh_raw[3, 3] = 1, 1, 2   # subap (1,1): x (-0.5+0.5+1)/4, y (-0.5-0.5+1)/4
+    sh_expect = [0.5, -0.25, -0.5, 0.5, 0.25, 0.0]
+    py = pyr_desc(2, valid=np.array([[1, 1], [0, 1]], np.uint8))
+    py_raw = np.zeros((8, 8), np.uint16)
+    A, B, C, D = (1, 1), (1, 5), (5, 1), (5, 5)     # (row, col) origins of the four pupil images
+    py_raw[A[0], A[1]] = 4                          # pixel (0,0): A only -> (1, 1)
+    py_raw[A[0], A[1] + 1], py_raw[B[0], B[1] + 1] = 1, 3   # pixel (0,1): A 1, B 3 -> ((1-3)/4, (1+3)/4)
+    py_raw[A[0] + 1, A[1]] = 5                      # pixel (1,0): invalid
+    py_raw[A[0] + 1, A[1] + 1], py_raw[C[0] + 1, C[1] + 1] = 1, 3   # pixel (1,1): A 1, C 3 -> (1, -0.5)
+    py_expect = [1.0, 1.0, -0.5, 1.0, 1.0, -0.5]
+    ref = np.arange(12) / 8.0
+    s = orc.frame_slopes(dict(wfs=[sh, py], ref_slopes=ref), [sh_raw, py_raw])
+    assert s.tolist() == (np.array(sh_expect + py_expect) - ref).tolist()
+    s = orc.frame_slopes(dict(wfs=[py, sh], ref_slopes=None), [py_raw, sh_raw])
+    assert s.tolist() == py_expect + sh_expect
+
+
+def test_oracle_loop_explicit_polc_clip_hand_values():
+    # D = 0, dyadic values: a_k = clip((1 - leak - g) a_{k-1} + g y) with (1 - leak - g) = 1/4
+    n = 4
+    raw = np.zeros((n, n), np.uint16)
+    raw[0, 3] = 10                                   # slopes (1.5, -1.5)
+    M = np.array([[4.0, -4.0], [-4.0, 4.0], [0.5, 0.5]], np.float32)   # y = M s = (12, -12, 0)
+    cfg = dict(wfs=[sh_desc(n)], M=M, gain=0.5, leak=0.25, ref_slopes=None, polc="explicit",
+               D=np.zeros((2, 3), np.float32), clip=(-2.0, 3.0))
+    loop = orc.OracleLoop(cfg)
+    for _ in range(2):                               # unclipped: (6, -6, 0) then (6.75, -6.5, 0)
+        s, a = loop.step([raw])
+        assert s.tolist() == [1.5, -1.5]
+        assert a.tolist() == [3.0, -2.0, 0.0]
+    # an all-zero frame gives y = 0: a = clip(a / 4), inside the bounds
+    s, a = loop.step([np.zeros((n, n), np.uint16)])
+    assert a.tolist() == [0.75, -0.5, 0.0]
+
+
+def test_oracle_loop_explicit_polc_with_clip_equals_implicit_with_clip():
+    # P = M D - I makes the two forms the same update; clipping the same quantity
+    # and feeding the clipped state back (D a or P a) keeps them equal.
+    rng = np.random.default_rng(23)
+    imp_cfg, exp_cfg, M, D = _polc_cfgs(rng)
+    imp_cfg["clip"] = exp_cfg["clip"] = (-0.3, 0.2)
+    imp, exp = orc.OracleLoop(imp_cfg), orc.OracleLoop(exp_cfg)
+    hit = 0
+    for _ in range(10):
+        raw = rng.integers(0, 50, size=(8, 8)).astype(np.uint16)
+        _, a_i = imp.step([raw])
+        _, a_e = exp.step([raw])
+        assert np.allclose(a_e, a_i, rtol=0, atol=1e-12)
+        assert a_e.min() >= -0.3 and a_e.max() <= 0.2
+        hit += int(np.sum((a_e == -0.3) | (a_e == 0.2)))
+    assert hit > 0                                    # the clip was active
