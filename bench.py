@@ -138,13 +138,26 @@ def code_text(src):
     return re.sub(r"\s+", "", src)
 
 
+KERNEL_SOURCES = ("rtc_kernels.cu", "rtc_internal.h", "rtc_runtime.cu")
+
+
 def kernel_source_hash(texts=None):
-    """Hash of the kernel sources (comments and whitespace ignored), recorded beside the
-    ncu figures so that they are reported only for the kernels they were taken on."""
+    """Hash of what decides the kernels' memory traffic: the kernel and runtime sources
+    (the runtime lays out the matrix blocks and picks the launches) and the build script
+    with its compiler flags and tuning macros, comments and whitespace ignored; recorded
+    beside the ncu figures so that they are reported only for the build they were taken
+    on.  A library named by RTC_LIBRARY (another build) never matches."""
+    default = texts is None
+    if default:
+        csrc = os.path.join(ROOT, "paper_1903_01852_gb300", "csrc")
+        texts = {f: open(os.path.join(csrc, f)).read() for f in KERNEL_SOURCES}
+        texts["build.py"] = open(os.path.join(ROOT, "paper_1903_01852_gb300", "build.py")).read()
     h = hashlib.sha256()
-    for f in ("rtc_kernels.cu", "rtc_internal.h"):
-        src = texts[f] if texts else open(os.path.join(ROOT, "paper_1903_01852_gb300", "csrc", f)).read()
-        h.update(code_text(src).encode())
+    for name in sorted(texts):
+        h.update(name.encode())
+        h.update(code_text(texts[name]).encode())
+    if default and os.environ.get("RTC_LIBRARY"):
+        h.update(("library:" + os.path.abspath(os.environ["RTC_LIBRARY"])).encode())
     return h.hexdigest()[:16]
 
 
@@ -503,11 +516,19 @@ def reference_arm(args, world, rank):
     out = {"impl": "reference", "metric": METRIC, "value": st["p50"], "unit": "us", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": st["mean"] / 1e3,
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic (seeded)", "config": {"workload": WORKLOAD},
+           "data": "synthetic (seeded)", "config": bench_config(cfg, world),
            "latency_us": st,
            "cpu_baseline": {"value": st["p50"], "unit": "us", "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": st["p50"], "unit": "us", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def bench_config(cfg, world):
+    """The workload's configuration as both arms report it."""
+    return {"workload": WORKLOAD, "na": int(cfg["na"]), "ns": int(cfg["ns"]),
+            "frames": f"{FRAME_RING} distinct frames resident in HBM, cycled",
+            "l2": "inputs larger than L2: the 1.67 GB FP32 (0.83 GB BF16, 0.42 GB E4M3) matrix is streamed every frame",
+            "replicas": world}
 
 
 def ours_arm(args, world, rank, local):
@@ -544,28 +565,28 @@ def ours_arm(args, world, rank, local):
 
     sampler = ClockSampler(local)
     sampler.start()
-    out = {}
     loops = {}
+    fmts = ("f32", "bf16", "e4m3")
     try:
-        bcfg = bf16_config(cfg, rtc, torch)
-        cfgs = {"f32": cfg, "bf16": bcfg}
-        for name in ("f32", "bf16"):
+        cfgs = {"f32": cfg, "bf16": quant_config(cfg, rtc, torch, "bf16"), "e4m3": quant_config(cfg, rtc, torch, "e4m3")}
+        for name in fmts:
             # latency loops: the MVM starts while the slope kernel runs (frame-level events only)
             loops[name] = rtc.Loop(cfgs[name], device=local, timing=True, telemetry=True)
             # stage loops: slope and MVM kernels timed separately (serialised) for the MVM bandwidth
             loops[name + "_stage"] = rtc.Loop(cfgs[name], device=local, stage_timing=True, telemetry=True)
+        for name in ("f32", "bf16"):
             # host-clock loops (paced and end-to-end): no CUDA events, whose records would add host
             # time before the launches that matter
             loops[name + "_host"] = rtc.Loop(cfgs[name], device=local, telemetry=True, updatable=(name == "f32"))
         fid = 1
         # 1) timed region: K unpaced steps, frames resident in HBM (device events around the region)
         ms_total, ids, _, fid = run_unpaced(loops["f32"], dev_frames, args.steps, args.warmup, torch, sampler, fid)
-        # per-frame latencies and per-kernel stage times, FP32 and BF16
+        # per-frame latencies (event-timed, 2x10^4 frames each) and per-kernel stage times, every format
         per, stg = {}, {}
-        for name in ("f32", "bf16"):
-            per[name], fid = run_unpaced_timed(loops[name], dev_frames, args.steps, args.warmup, sampler, fid)
-            stg[name], fid = run_unpaced_timed(loops[name + "_stage"], dev_frames, args.steps, args.warmup, sampler,
-                                               fid)
+        for name in fmts:
+            per[name], fid = run_unpaced_timed(loops[name], dev_frames, args.latency_frames, args.warmup, sampler, fid)
+            stg[name], fid = run_unpaced_timed(loops[name + "_stage"], dev_frames, args.stage_frames, args.warmup,
+                                               sampler, fid)
         # 2) end-to-end through the C ABI from page-locked host buffers (unpaced, whole frames):
         #    graph mode (the public path with the least host work), and rtc_process_frame
         with rtc.Loop(cfg, device=local, telemetry=True, graphs=True, ring=len(frames)) as gl:
@@ -582,7 +603,18 @@ def ours_arm(args, world, rank, local):
                                             args.paced_warmup, sampler, fid, paced=True, swap=(1.0, {"M": cfg["M"]}))
         swap_info["latency_us_other_frames"] = stats(lat, 1e6 / PACED_HZ)
         infos = {n: loops[n].info() for n in loops}
+        for lp in loops.values():
+            lp.close()
+        loops = {}
+        # 5) the serving mix (LTAO + MCAO + 2 ELT SCAO, BF16, graph mode), per-loop latency
+        mix = None
+        if rank == 0 and args.mix_seconds > 0:
+            sampler.mark(True)
+            mix = serving_mix(args.mix_seconds, with_alone=False)
+            sampler.mark(False)
     finally:
+        for lp in loops.values():
+            lp.close()
         sampler.stop()
     lat = {n: stats([r["latency_us"] for r in per[n]]) for n in per}
     mvm_us = {n: statistics.median([r["mvm_us"] for r in stg[n]]) for n in stg}
@@ -607,13 +639,10 @@ def ours_arm(args, world, rank, local):
                 if k >= 1:
                     r = cmds_ref[k - 1]
                     errs.append(float(np.max(np.abs(a - r)) / np.max(np.abs(r))))
-        parity = {"frames": len(errs), "max_rel_err_commands": max(errs), "tol": 1e-5,
-                  "norm": "max|a - a_oracle| / max|a_oracle| per frame, FP32 path, float64 oracle"}
+        parity = {"frames": len(errs), "max_rel_err_commands": max(errs), "tol": 1e-5}
         cpu["stages_1_thread"] = oracle_stages(cfg, frames)
         cpu["stages_all_cores"] = oracle_stages_all_cores()
         cpu["host"] = host_cpu()
-    for l in loops.values():
-        l.close()
 
     # max over ranks (replicas: the slowest replica's latencies)
     vals = max_over_ranks([lat["f32"]["p50"], ms_total / args.steps, float(np.median(e2e_lat))], world, "cuda")
@@ -625,30 +654,20 @@ def ours_arm(args, world, rank, local):
         "metric": METRIC, "value": vals[0], "unit": "us", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": vals[1], "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded frames, random-init matrices)",
-        "config": {"workload": WORKLOAD, "na": infos["f32"]["na"], "ns": infos["f32"]["ns"],
-                   "frames": "8 distinct frames resident in HBM, cycled",
-                   "l2": "inputs larger than L2: the 1.67 GB FP32 (0.83 GB BF16) matrix is streamed every frame",
-                   "replicas": world},
+        "config": bench_config(cfg, world),
         "latency_us": lat["f32"],
         "bf16": {"latency_us": lat["bf16"], "stage_us": stage["bf16"]},
+        "e4m3": {"latency_us": lat["e4m3"], "stage_us": stage["e4m3"]},
         "stage_us": stage["f32"],
-        "mvm_gbs": {"f32": gbs["f32"], "bf16": gbs["bf16"]},
-        "mvm_frac_of_hbm": {"f32": gbs["f32"] / peak, "bf16": gbs["bf16"] / peak, "peak": f"{peak_kind} {peak} GB/s"},
-        "paced": {"definition": "last chunk submitted (last pixel in) -> commands returned, host clock; "
-                                f"{PACED_HZ:.0f} Hz, {READOUT_MS} ms readout over {NCHUNKS} row chunks per LGS camera, "
-                                f"pixels from page-locked host memory; {args.paced_frames} frames after "
-                                f"{args.paced_warmup} warm-up frames per format; loops without CUDA event timing",
-                  **paced},
-        "swap": {"definition": "paced FP32 frames while a second thread re-uploads the 1.67 GB control matrix "
-                               "into the shadow buffer every 1 s (rtc_update); the first frame after each upload "
-                               "swaps pointers at its start (Section 3.2's double buffer)", **swap_info},
+        "mvm_gbs": gbs,
+        "mvm_frac_of_hbm": {n: gbs[n] / peak for n in gbs},
+        "mvm_frames": args.stage_frames,
+        "paced": paced,
+        "swap": swap_info,
         "e2e": {"value": vals[2], "unit": "us", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": 4 * (infos["f32"]["na"] + infos["f32"]["ns"]),
-                "definition": "rtc_submit_frame_graph entry -> rtc_get_commands returned, host clock, unpaced; "
-                              "each frame in the loop's page-locked input buffers (8 ring slots holding the 8 "
-                              "frames), read in place by the slope kernel over NVLink-C2C; commands and slope "
-                              "telemetry written to page-locked host memory", "latency_us": stats(e2e_lat),
-                "process_frame_latency_us": stats(pf_lat)},
+                "latency_us": stats(e2e_lat), "process_frame_latency_us": stats(pf_lat)},
+        "serving_mix": mix,
         "roofline": {"bound": "hbm", "achieved": gbs["f32"], "peak": peak, "unit": "GB/s",
                      "frac": gbs["f32"] / peak, "traffic": traffic, "kernel": "gemv_kernel<f32> (reconstruction MVM)",
                      "algorithmic_bytes_per_launch": mb, "peak_kind": peak_kind},
@@ -727,16 +746,15 @@ SERVING_LOOPS = (("ltao", "ltao", 500.0), ("mcao", "mcao", 500.0), ("scao_a", "e
                  ("scao_b", "elt_scao_sh", 1000.0))
 
 
-def serving_arm(args):
+def serving_mix(dur, with_alone=True):
     """Serving mix on one GPU: a HARMONI-like LTAO loop, the MAORY-like MCAO loop and two ELT SCAO SH
     loops resident at once (BF16 matrices, graph mode), admitted by HBM footprint into one server;
     frames arrive at 500 Hz (LTAO, MCAO) and 1 kHz (SCAO) with seeded staggered phases and +-20 us
-    uniform jitter.  Latency per loop = rtc_server_submit -> commands written (the server's poller).
-    Each loop is also run alone with the same arrivals for comparison."""
+    uniform jitter for dur seconds.  Latency per loop = rtc_server_submit -> commands written (the
+    server's poller).  with_alone: each loop is also run alone with the same arrivals."""
     import torch
     from paper_1903_01852_gb300 import binding as rtc
     from paper_1903_01852_gb300 import synth
-    torch.cuda.set_device(0)
     rng = np.random.default_rng(4242)
     cfgs, frames = {}, {}
     for name, conf, _ in SERVING_LOOPS:
@@ -745,7 +763,6 @@ def serving_arm(args):
         frames[name] = synth.draw_frames(c, 2, seed=6000 + len(frames))
     foot = {n: rtc.footprint(cfgs[n], flags=rtc.RTC_FLAG_GRAPHS)[0] for n in cfgs}
     budget = int(sum(foot.values()) * 1.02)
-    dur = args.serving_seconds
 
     def schedule(names):
         ev = []
@@ -797,16 +814,23 @@ def serving_arm(args):
 
     names = [n for n, _, _ in SERVING_LOOPS]
     mix, usage, fps = run(names)
-    alone = {n: run([n])[0][n] for n in names}
+    alone = {n: run([n])[0][n] for n in names} if with_alone else None
     keys = ("p50_us", "p99_us", "p999_us", "mean_us", "jitter_rms_us", "max_us", "frames")
+    loops = {}
+    for n, conf, hz in SERVING_LOOPS:
+        loops[n] = {"rate_hz": hz, "config": conf, "mix": {k: mix[n][k] for k in keys}}
+        if alone:
+            loops[n]["alone"] = {k: alone[n][k] for k in keys}
+    return {"seconds": dur, "frames_per_s": fps, "budget_bytes": budget, "admitted_bytes": usage["used"],
+            "loops": loops}
+
+
+def serving_arm(args):
+    """The serving mix alone (--serving), each loop also run alone, one JSON line."""
+    import torch
+    torch.cuda.set_device(0)
     out = {"mode": "serving", "metric": "per-loop frame latency, serving mix on one GB300 (BF16 matrices, graphs)",
-           "unit": "us", "seconds": dur, "frames_per_s": fps, "budget_bytes": budget,
-           "admitted_bytes": usage["used"], "footprint_bytes": foot,
-           "loops": {n: {"rate_hz": hz, "config": conf, "mix": {k: mix[n][k] for k in keys},
-                         "alone": {k: alone[n][k] for k in keys}} for n, conf, hz in SERVING_LOOPS},
-           "definition": "rtc_server_submit entry -> the loop's page-locked completion word set (server poller, "
-                         "host clock); arrivals at 500 Hz / 1 kHz, seeded phases, +-20 us jitter; 'alone' = the "
-                         "same loop and arrivals without the others"}
+           "unit": "us", **serving_mix(args.serving_seconds, with_alone=True)}
     print(json.dumps(out), flush=True)
 
 
@@ -949,6 +973,11 @@ def main():
     ap.add_argument("--swap-frames", type=int, default=2500, help="paced frames of the parameter-swap run")
     ap.add_argument("--serving", action="store_true", help="serving mix (LTAO + MCAO + 2 SCAO) instead")
     ap.add_argument("--serving-seconds", type=float, default=4.0)
+    ap.add_argument("--latency-frames", type=int, default=20000,
+                    help="event-timed frames per matrix format for the latency statistics")
+    ap.add_argument("--stage-frames", type=int, default=300, help="stage-timed frames per format for the MVM GB/s")
+    ap.add_argument("--mix-seconds", type=float, default=3.0,
+                    help="seconds of the serving mix in the default run (0: leave it out)")
     ap.add_argument("--variants", action="store_true",
                     help="POLC forms, telemetry streaming, chunking depth, pyramid normalisation instead")
     ap.add_argument("--variant-frames", type=int, default=3000, help="paced frames per --variants case")
