@@ -82,6 +82,9 @@ extern "C" {
 #define RTC_FLAG_GRAPHS    16u /* page-locked input frames per ring slot and one captured CUDA
                                   graph per slot (rtc_next_frame_buffers, rtc_submit_frame_graph);
                                   excludes RTC_FLAG_UPDATABLE and RTC_FLAG_STAGE_TIMING */
+#define RTC_FLAG_PARTIAL   32u /* a shard of a loop split by WFS (rtc_master): the loop computes
+                                  only its WFS's partial reconstruction and no control law;
+                                  polc->P and polc->D must be NULL */
 
 #define RTC_MAX_WFS 16
 
@@ -506,6 +509,66 @@ int rtc_server_usage(rtc_server* server, uint64_t* used_bytes, uint64_t* budget_
                      int32_t* queued);
 /* Text of the server's last failure.  Never NULL. */
 const char* rtc_server_last_error(const rtc_server* server);
+
+/* ---- per-WFS sharding (Section 3, Fig. mcaoltao_test) ---------------------
+ *
+ * The paper runs one reconstruction node per WFS and a master that adds the
+ * nodes' partial DM commands and applies the control law.  A loop created with
+ * RTC_FLAG_PARTIAL is such a node: for its WFS (their columns of the control
+ * matrix, in their slope order) each frame gives the partial reconstruction
+ *   y[r] = row_scale[r] * sum_j M[r][j] s[j]
+ * in place of commands: rtc_get_commands returns y, and the loop's state, POLC
+ * term and clip are unused.  A master holds the control law of the whole loop:
+ *   a_k = (1 - leak) a_{k-1} + gain (sum_k y_k + q_{k-1}), optional clip,
+ *   q_k = P a_k (implicit POLC, computed after the commands),
+ * with the shards' partials added in shard order. */
+
+/* Where a RTC_FLAG_PARTIAL loop's kernel also writes y (na floats) each frame:
+ * device memory of any GPU the loop's device can write (the caller enables
+ * peer access between different GPUs), typically rtc_master_input of a
+ * master; NULL stops it.  Takes effect for frames submitted after the call
+ * (graph mode included: the pointer is read by the kernel each frame).  The
+ * caller keeps the buffer valid while frames run.  RTC_EINVAL if the loop is
+ * not RTC_FLAG_PARTIAL or the pointer is not device memory. */
+int rtc_set_partial_output(rtc_loop* loop, float* device_ptr);
+
+typedef struct rtc_master rtc_master;   /* opaque */
+
+typedef struct rtc_master_desc {
+    int32_t device;              /* CUDA device of the master */
+    int32_t na;                  /* actuators */
+    int32_t nshards;             /* partial inputs, 1..RTC_MAX_WFS */
+    const rtc_polc* polc;        /* P (na x na, optional), gain, leak, a0, clip; mode must be
+                                    RTC_POLC_IMPLICIT and D NULL */
+} rtc_master_desc;
+
+/* Create a master: device buffers for nshards partial inputs of na floats
+ * (zero), the state a (a0 or 0), P and q = P a0, a page-locked command buffer.
+ * RTC_EINVAL for bad sizes or a non-finite P / a0; RTC_ENOMEM, RTC_ECUDA. */
+int rtc_master_create(const rtc_master_desc* desc, rtc_master** out);
+/* Device address of input `shard` (na floats on the master's device), for
+ * rtc_set_partial_output or the caller's own copies.  Owned by the master. */
+int rtc_master_input(rtc_master* master, int32_t shard, float** device_ptr);
+/* Copy na floats (host or device memory) into input `shard`, ordered before
+ * the next rtc_master_step (for partials that arrive from another process or
+ * node).  Pageable host data is copied before the call returns. */
+int rtc_master_set_input(rtc_master* master, int32_t shard, const float* src, size_t n);
+/* Apply the control law to the inputs, which must hold frame frame_id's partials
+ * (the caller has seen each shard's frame complete, e.g. by its
+ * rtc_get_commands, or has copied them in with work ordered before this call):
+ * commands, then their copy to page-locked host memory, then the POLC product
+ * for the next frame, on the master's stream.  frame_id must increase
+ * (RTC_EORDER otherwise).  Asynchronous. */
+int rtc_master_step(rtc_master* master, uint64_t frame_id);
+/* The commands of the last stepped frame (n >= na floats), waiting up to
+ * timeout_us (negative: no limit) for them; RTC_ETIMEDOUT, RTC_ENOENT before
+ * the first step. */
+int rtc_master_get_commands(rtc_master* master, float* out, size_t n, uint64_t* frame_id, int64_t timeout_us);
+/* Wait for the master's work, then release it. */
+int rtc_master_destroy(rtc_master* master);
+/* Text of the master's last failure (or of the last rtc_master_create failure
+ * for NULL).  Never NULL. */
+const char* rtc_master_last_error(const rtc_master* master);
 
 /* ---- allocation-free reconstruction step ------------------------------ */
 

@@ -25,6 +25,7 @@ RTC_THRESH_SUBTRACT, RTC_THRESH_CLIP = 0, 1
 RTC_NORM_LOCAL, RTC_NORM_GLOBAL = 0, 1
 RTC_POLC_IMPLICIT, RTC_POLC_EXPLICIT = 0, 1
 RTC_FLAG_TIMING, RTC_FLAG_TELEMETRY, RTC_FLAG_STAGE_TIMING, RTC_FLAG_UPDATABLE, RTC_FLAG_GRAPHS = 1, 2, 4, 8, 16
+RTC_FLAG_PARTIAL = 32
 RTC_MAX_WFS = 16
 RTC_TEL_SLOPES, RTC_TEL_COMMANDS, RTC_TEL_PARTIALS = 1, 2, 4
 DTYPES = {"f32": RTC_F32, "bf16": RTC_BF16, "e4m3": RTC_E4M3}
@@ -106,6 +107,10 @@ class rtc_info(C.Structure):
                 ("frames_overrun", C.c_uint64), ("swaps", C.c_uint64)]
 
 
+class rtc_master_desc(C.Structure):
+    _fields_ = [("device", C.c_int32), ("na", C.c_int32), ("nshards", C.c_int32), ("polc", C.POINTER(rtc_polc))]
+
+
 # (name, restype, argtypes) of every entry point declared in include/rtc.h
 SIGNATURES = [
     ("rtc_create", C.c_int, [C.POINTER(rtc_geometry), C.POINTER(rtc_calib), C.POINTER(rtc_cmat),
@@ -145,6 +150,14 @@ SIGNATURES = [
     ("rtc_server_last_error", C.c_char_p, [C.c_void_p]),
     ("rtc_quantize_rows", C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_size_t, C.c_void_p,
                                     C.c_void_p, C.c_void_p]),
+    ("rtc_set_partial_output", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("rtc_master_create", C.c_int, [C.POINTER(rtc_master_desc), C.POINTER(C.c_void_p)]),
+    ("rtc_master_input", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]),
+    ("rtc_master_set_input", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_size_t]),
+    ("rtc_master_step", C.c_int, [C.c_void_p, C.c_uint64]),
+    ("rtc_master_get_commands", C.c_int, [C.c_void_p, f32p, C.c_size_t, C.POINTER(C.c_uint64), C.c_int64]),
+    ("rtc_master_destroy", C.c_int, [C.c_void_p]),
+    ("rtc_master_last_error", C.c_char_p, [C.c_void_p]),
     ("rtc_reconstruct_noalloc", C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p,
                                           C.c_void_p, C.c_void_p, C.c_void_p, C.c_float, C.c_float, C.c_void_p]),
 ]
@@ -280,14 +293,14 @@ class Loop:
 
     def __init__(self, cfg, device=0, timing=False, telemetry=False, ring=4, stage_timing=False, updatable=False,
                  graphs=False, tel_depth=0, tel_streams=RTC_TEL_SLOPES | RTC_TEL_COMMANDS, tel_decimate=1,
-                 _handle=None):
+                 partial=False, _handle=None):
         self.cfg = cfg
         self.na = int(cfg["na"])
         self._owned = _handle is None
         if _handle is None:
             flags = ((RTC_FLAG_TIMING if timing or stage_timing else 0) | (RTC_FLAG_TELEMETRY if telemetry else 0)
                      | (RTC_FLAG_STAGE_TIMING if stage_timing else 0) | (RTC_FLAG_UPDATABLE if updatable else 0)
-                     | (RTC_FLAG_GRAPHS if graphs else 0))
+                     | (RTC_FLAG_GRAPHS if graphs else 0) | (RTC_FLAG_PARTIAL if partial else 0))
             st = describe(cfg, device, flags, ring, (tel_depth, tel_streams, tel_decimate))
             h = C.c_void_p()
             _check(lib.rtc_create(C.byref(st.geo), C.byref(st.cal), C.byref(st.cm), C.byref(st.pol), C.byref(h)))
@@ -478,6 +491,80 @@ class Loop:
     @property
     def last_error(self):
         return _err(self._h)
+
+
+def set_partial_output(loop, ptr):
+    """rtc_set_partial_output: a RTC_FLAG_PARTIAL loop also writes its partial
+    reconstruction to device address ptr (int, or None to stop)."""
+    _check(lib.rtc_set_partial_output(loop._h, ptr), loop._h)
+
+
+class Master:
+    """The control law of a loop split by WFS (rtc_master_*): adds the shards'
+    partial reconstructions in shard order, POLC term, leaky integrator."""
+
+    def __init__(self, cfg, nshards, device=0):
+        self.na = int(cfg["na"])
+        st = describe(dict(cfg, wfs=cfg.get("wfs") or [], M=np.zeros((self.na, 0), np.float32)), device)
+        self._keep = st
+        d = rtc_master_desc(device, self.na, int(nshards), C.pointer(st.pol))
+        h = C.c_void_p()
+        rc = lib.rtc_master_create(C.byref(d), C.byref(h))
+        if rc != RTC_OK:
+            raise RtcError(rc, lib.rtc_master_last_error(None).decode(errors="replace"))
+        self._h = h
+        self._cmd = np.empty(self.na, np.float32)
+
+    def _err(self):
+        return lib.rtc_master_last_error(self._h).decode(errors="replace")
+
+    def input(self, shard):
+        p = C.c_void_p()
+        rc = lib.rtc_master_input(self._h, shard, C.byref(p))
+        if rc != RTC_OK:
+            raise RtcError(rc, self._err())
+        return p.value
+
+    def set_input(self, shard, y):
+        """Copy a shard's partial (numpy float32 [na], or a device pointer) into input `shard`."""
+        if isinstance(y, int):
+            rc = lib.rtc_master_set_input(self._h, shard, y, self.na)
+        else:
+            y = np.ascontiguousarray(y, dtype=np.float32)
+            rc = lib.rtc_master_set_input(self._h, shard, y.ctypes.data, y.size)
+        if rc != RTC_OK:
+            raise RtcError(rc, self._err())
+
+    def step(self, frame_id):
+        rc = lib.rtc_master_step(self._h, frame_id)
+        if rc != RTC_OK:
+            raise RtcError(rc, self._err())
+
+    def get_commands(self, timeout_us=-1):
+        fid = C.c_uint64()
+        rc = lib.rtc_master_get_commands(self._h, self._cmd.ctypes.data_as(f32p), self.na, C.byref(fid), timeout_us)
+        if rc == RTC_ETIMEDOUT:
+            raise TimeoutError(self._err())
+        if rc != RTC_OK:
+            raise RtcError(rc, self._err())
+        return fid.value, self._cmd.copy()
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib.rtc_master_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def quantize_rows(M, fmt, stream=None):

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librtc.so")
-SOURCES = ["rtc_kernels.cu", "rtc_runtime.cu", "rtc_server.cu", "rtc_noalloc.cu"]
+SOURCES = ["rtc_kernels.cu", "rtc_runtime.cu", "rtc_server.cu", "rtc_noalloc.cu", "rtc_master.cu"]
 HEADERS = [os.path.join(CSRC, "rtc_internal.h"), os.path.join(ROOT, "include", "rtc.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -81,6 +81,9 @@ struct FinaliseArgs {
                                     // host before the launch, so a captured graph can be replayed)
     unsigned long long* t_done;     // device word of the slot: GPU global time (ns) when the commands
                                     // were complete, or NULL
+    int partial;                    // shard loop (RTC_FLAG_PARTIAL): cmd gets the partial reconstruction,
+                                    // no control law
+    float* const* pout;             // device word: where else a shard writes it (NULL: nowhere)
 };
 
 // Frame pointers for one launch; pitch in uint16 elements.  px[w] holds pixel

@@ -642,6 +642,12 @@ __device__ void finalise_tile(const FinaliseArgs& f, const float* __restrict__ p
 #pragma unroll
         for (int k = 0; k < kGemvWarps; ++k) t += red[k][lane];
         if (f.scale) t *= f.scale[r];
+        if (f.partial) {               // a shard: its partial reconstruction, for a master to add
+            f.cmd[r] = t;
+            float* const po = *f.pout;
+            if (po) po[r] = t;
+            return;
+        }
         const float w = t + f.q[r];
         float v = fmaf(f.gain, w, f.oml * f.a[r]);
         if (f.clip) v = fminf(fmaxf(v, f.amin), f.amax);

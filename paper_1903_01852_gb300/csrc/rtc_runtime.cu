@@ -52,6 +52,8 @@ struct rtc_loop {
     int clip = 0;
     bool has_polc = false, timing = false, telemetry = false, stage_timing = false;
     bool explicit_polc = false;     // s + D a formed before the reconstruction (RTC_POLC_EXPLICIT)
+    bool partial = false;           // RTC_FLAG_PARTIAL: a shard, partial reconstruction only
+    float** d_pout = nullptr;       // device word: where else the shard writes its partial
 
     // host plans
     std::vector<rtc_wfs> wfs;
@@ -439,6 +441,9 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
     L->amin = P->amin;
     L->amax = P->amax;
     L->graphs = (G->flags & RTC_FLAG_GRAPHS) != 0;
+    L->partial = (G->flags & RTC_FLAG_PARTIAL) != 0;
+    if (L->partial && (P->P || P->D || L->explicit_polc))
+        return fail(L, RTC_EINVAL, "a RTC_FLAG_PARTIAL loop takes no POLC matrix (the master applies it)");
     if (G->tel_depth < 0 || G->tel_depth > (1 << 20)) return fail(L, RTC_EINVAL, "tel_depth must be in [0, 2^20]");
     if (G->tel_decimate < 0) return fail(L, RTC_EINVAL, "tel_decimate must be >= 0");
     if (G->tel_streams & ~(RTC_TEL_SLOPES | RTC_TEL_COMMANDS | RTC_TEL_PARTIALS))
@@ -847,6 +852,8 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
     }
     TRY(dev_alloc(L, &L->d_tiles_done, sizeof(unsigned)));
     CK(L, cudaMemset(L->d_tiles_done, 0, sizeof(unsigned)));
+    TRY(dev_alloc(L, &L->d_pout, sizeof(float*)));
+    CK(L, cudaMemset(L->d_pout, 0, sizeof(float*)));
     L->slots.resize(L->ring);
     const unsigned evflags = L->timing ? cudaEventDefault : cudaEventDisableTiming;
     for (auto& s : L->slots) {
@@ -1056,6 +1063,8 @@ FinaliseArgs fin_args(rtc_loop* L) {
     f.done_flag = L->d_done + L->cur_slot;
     f.seq = L->d_seq + L->cur_slot;
     f.t_done = L->d_tdone + L->cur_slot;
+    f.partial = L->partial ? 1 : 0;
+    f.pout = L->d_pout;
     return f;
 }
 
@@ -1854,6 +1863,26 @@ int rtc_check_guards(rtc_loop* L, int32_t* corrupted) {
 int rtc_get_stream(rtc_loop* L, void** stream) {
     if (!L || !stream) return fail(L, RTC_EINVAL, "loop and stream are required");
     *stream = static_cast<void*>(L->st);
+    return RTC_OK;
+}
+
+int rtc_set_partial_output(rtc_loop* L, float* device_ptr) {
+    if (!L) return fail(nullptr, RTC_EINVAL, "loop is NULL");
+    if (!L->partial) return fail(L, RTC_EINVAL, "the loop was not created with RTC_FLAG_PARTIAL");
+    TRY(use_device(L));
+    if (device_ptr) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, device_ptr) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(L, RTC_EINVAL, "partial output is not device memory");
+        }
+        if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+            return fail(L, RTC_EINVAL, "partial output is not device memory");
+    }
+    // frames already queued keep the pointer they read; the word is written in stream order
+    for (cudaStream_t w : L->st_w) CK(L, cudaStreamSynchronize(w));
+    CK(L, cudaStreamSynchronize(L->st));
+    CK(L, cudaMemcpy(L->d_pout, &device_ptr, sizeof(float*), cudaMemcpyHostToDevice));
     return RTC_OK;
 }
 

@@ -86,7 +86,8 @@ def test_structs_mirror_the_header_layout(rtc, tmp_path):
     if shutil.which("gcc") is None:
         pytest.skip("gcc not available")
     structs = [rtc.rtc_wfs, rtc.rtc_geometry, rtc.rtc_calib, rtc.rtc_cmat, rtc.rtc_polc, rtc.rtc_chunk,
-               rtc.rtc_timing, rtc.rtc_tel_record, rtc.rtc_tel_stream_stats, rtc.rtc_update_desc, rtc.rtc_server_loop_info, rtc.rtc_info]
+               rtc.rtc_timing, rtc.rtc_tel_record, rtc.rtc_tel_stream_stats, rtc.rtc_update_desc, rtc.rtc_server_loop_info, rtc.rtc_info,
+               rtc.rtc_master_desc]
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "rtc.h"', "int main(void) {"]
     for st in structs:
         n = st.__name__
@@ -174,3 +175,30 @@ def test_graph_mode_excludes_stage_timing_without_gpu(rtc):
     assert rtc.footprint(cfg, flags=rtc.RTC_FLAG_GRAPHS | rtc.RTC_FLAG_TIMING)[0] > 0
     with pytest.raises(rtc.RtcError, match="STAGE_TIMING"):
         rtc.footprint(cfg, flags=rtc.RTC_FLAG_GRAPHS | rtc.RTC_FLAG_STAGE_TIMING)
+
+
+def test_partial_loops_and_master_validation_without_gpu(rtc):
+    import numpy as np
+    from paper_1903_01852_gb300 import synth
+    cfg = synth.make_config("scao_small", polc=True)
+    with pytest.raises(rtc.RtcError, match="no POLC matrix"):
+        rtc.footprint(cfg, flags=rtc.RTC_FLAG_PARTIAL)            # a shard leaves POLC to the master
+    assert rtc.footprint(dict(cfg, P=None), flags=rtc.RTC_FLAG_PARTIAL)[0] > 0
+    assert rtc.lib.rtc_set_partial_output(None, None) == rtc.RTC_EINVAL
+    h = C.c_void_p()
+    assert rtc.lib.rtc_master_create(None, C.byref(h)) == rtc.RTC_EINVAL and h.value is None
+    pol = rtc.rtc_polc(None, 0, None, 0.5, 0.01, None, 0, 0.0, 0.0, 0, None, 0, None)
+    for na, nshards in ((0, 1), (4, 0), (4, rtc.RTC_MAX_WFS + 1)):
+        d = rtc.rtc_master_desc(0, na, nshards, C.pointer(pol))
+        assert rtc.lib.rtc_master_create(C.byref(d), C.byref(h)) == rtc.RTC_EINVAL
+    pol.mode = rtc.RTC_POLC_EXPLICIT
+    d = rtc.rtc_master_desc(0, 4, 2, C.pointer(pol))
+    assert rtc.lib.rtc_master_create(C.byref(d), C.byref(h)) == rtc.RTC_EINVAL
+    assert b"implicit POLC only" in rtc.lib.rtc_master_last_error(None)
+    pol.mode = rtc.RTC_POLC_IMPLICIT
+    P = np.full((4, 4), np.nan, np.float32)
+    pol.P = P.ctypes.data
+    assert rtc.lib.rtc_master_create(C.byref(d), C.byref(h)) == rtc.RTC_EINVAL
+    assert b"NaN" in rtc.lib.rtc_master_last_error(None)
+    assert rtc.lib.rtc_master_step(None, 1) == rtc.RTC_EINVAL
+    assert rtc.lib.rtc_master_destroy(None) == rtc.RTC_OK
