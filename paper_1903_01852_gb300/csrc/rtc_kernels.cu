@@ -851,8 +851,13 @@ cudaError_t launch_maybe_pdl(K kernel, dim3 grid, const GemvArgs& a, bool pdl, c
     return cudaLaunchKernelEx(&cfg, kernel, a);
 }
 
+// Launches too small for RTC_GEMV_MIN_WAVES waves of 8 CTAs per SM at four rows
+// per warp take fewer rows per warp.  Two waves: the ELT SCAO MVM (5316 x 8608,
+// 8 blocks) runs one row per warp in 5344 CTAs, and more of them start while the
+// slope kernel runs and prefetch their tiles into L2 (frame latency 43.3 against
+// 45.1 us with one wave, although the MVM alone is slower: 40.6 against 36.5 us).
 #ifndef RTC_GEMV_MIN_WAVES
-#define RTC_GEMV_MIN_WAVES 1
+#define RTC_GEMV_MIN_WAVES 2
 #endif
 
 template <int DT, int U, int RI>
