@@ -746,20 +746,23 @@ SERVING_LOOPS = (("ltao", "ltao", 500.0), ("mcao", "mcao", 500.0), ("scao_a", "e
                  ("scao_b", "elt_scao_sh", 1000.0))
 
 
-def serving_mix(dur, with_alone=True):
+def serving_mix(dur, with_alone=True, priorities=True):
     """Serving mix on one GPU: a HARMONI-like LTAO loop, the MAORY-like MCAO loop and two ELT SCAO SH
     loops resident at once (BF16 matrices, graph mode), admitted by HBM footprint into one server;
     frames arrive at 500 Hz (LTAO, MCAO) and 1 kHz (SCAO) with seeded staggered phases and +-20 us
     uniform jitter for dur seconds.  Latency per loop = rtc_server_submit -> commands written (the
-    server's poller).  with_alone: each loop is also run alone with the same arrivals."""
+    server's poller).  with_alone: each loop is also run alone with the same arrivals.
+    priorities: the 1 kHz loops' streams one priority level above the 500 Hz loops'
+    (rtc_geometry.priority), so their shorter frames get the SMs first."""
     import torch
     from paper_1903_01852_gb300 import binding as rtc
     from paper_1903_01852_gb300 import synth
     rng = np.random.default_rng(4242)
     cfgs, frames = {}, {}
-    for name, conf, _ in SERVING_LOOPS:
+    for name, conf, hz in SERVING_LOOPS:
         c = synth.make_config(conf, seed=5000 + len(cfgs))
         cfgs[name] = quant_config(c, rtc, torch, "bf16")
+        cfgs[name]["priority"] = (0 if hz >= 1000.0 else 1) if priorities else 0
         frames[name] = synth.draw_frames(c, 2, seed=6000 + len(frames))
     foot = {n: rtc.footprint(cfgs[n], flags=rtc.RTC_FLAG_GRAPHS)[0] for n in cfgs}
     budget = int(sum(foot.values()) * 1.02)
@@ -822,7 +825,7 @@ def serving_mix(dur, with_alone=True):
         if alone:
             loops[n]["alone"] = {k: alone[n][k] for k in keys}
     return {"seconds": dur, "frames_per_s": fps, "budget_bytes": budget, "admitted_bytes": usage["used"],
-            "loops": loops}
+            "priorities": "1 kHz loops above 500 Hz loops" if priorities else "all equal", "loops": loops}
 
 
 def serving_arm(args):

@@ -143,6 +143,11 @@ typedef struct rtc_geometry {
     int32_t tel_depth;           /* telemetry circular-buffer entries, 0 for none */
     uint32_t tel_streams;        /* RTC_TEL_* */
     int32_t tel_decimate;        /* record every n-th frame (0 is taken as 1) */
+    int32_t priority;            /* scheduling priority of the loop's streams among the loops on
+                                    its GPU: 0 (default) the highest, each step one level lower
+                                    (clamped to the device's lowest); a loop with a shorter frame
+                                    period given a higher priority gets the SMs first when frames
+                                    of several loops are on the GPU together (rtc_server) */
 } rtc_geometry;
 
 /* Pixel calibration (Section 2.2): c = (raw - dark) * flat, then the threshold.

@@ -46,7 +46,7 @@ class rtc_wfs(C.Structure):
 class rtc_geometry(C.Structure):
     _fields_ = [("nwfs", C.c_int32), ("wfs", C.POINTER(rtc_wfs)), ("device", C.c_int32),
                 ("flags", C.c_uint32), ("ring", C.c_int32), ("tel_depth", C.c_int32), ("tel_streams", C.c_uint32),
-                ("tel_decimate", C.c_int32)]
+                ("tel_decimate", C.c_int32), ("priority", C.c_int32)]
 
 
 class rtc_calib(C.Structure):
@@ -252,7 +252,8 @@ def describe(cfg, device=0, flags=0, ring=4, tel=(0, 0, 1)):
         keep += [d, f]
         darks[k] = _fptr(d)
         flats[k] = _fptr(f)
-    st.geo = rtc_geometry(len(wl), warr, device, flags, ring, int(tel[0]), int(tel[1]), int(tel[2]))
+    st.geo = rtc_geometry(len(wl), warr, device, flags, ring, int(tel[0]), int(tel[1]), int(tel[2]),
+                          int(cfg.get("priority", 0)))
     ref = _f32(cfg.get("ref_slopes"))
     st.cal = rtc_calib(darks, flats, thr.ctypes.data_as(f32p), mode.ctypes.data_as(C.POINTER(C.c_int32)), _fptr(ref))
     mdt = DTYPES[cfg.get("M_dtype", "f32")]

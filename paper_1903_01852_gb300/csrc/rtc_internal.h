@@ -103,6 +103,20 @@ struct BlockDev {
     int c0;                   // compact index of the block's first column
 };
 
+// Launch kernel<<<grid, block, smem, st>>>(args...) and return the launch's own
+// status: an error that earlier work of the calling thread left pending is
+// neither reported as this launch's nor cleared.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_kernel(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                          Args&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 size_t dtype_size(int dtype);
 int elems_per_16B(int dtype);
 

@@ -465,11 +465,8 @@ cudaError_t launch_slopes(const SlopeCta* ctas, int cta0, int nctas, const WfsDe
     a.counters = counters;
     a.fp = fp;
     std::copy(wfs, wfs + nwfs, a.wfs);
-    if (host_px)
-        slopes_kernel<true><<<nctas, kSlopeThreads, smem_bytes, st>>>(a);
-    else
-        slopes_kernel<false><<<nctas, kSlopeThreads, smem_bytes, st>>>(a);
-    return cudaGetLastError();
+    if (host_px) return launch_kernel(slopes_kernel<true>, dim3(nctas), dim3(kSlopeThreads), smem_bytes, st, a);
+    return launch_kernel(slopes_kernel<false>, dim3(nctas), dim3(kSlopeThreads), smem_bytes, st, a);
 }
 
 // ---------------------------------------------------------------------------
@@ -832,8 +829,7 @@ cudaError_t launch_telemetry(const TelArgs& t, cudaStream_t st) {
     if (t.streams & RTC_TEL_COMMANDS) ny += 1;
     if (t.streams & RTC_TEL_PARTIALS) ny += t.nwfs;
     const dim3 grid(4, (unsigned)std::max(ny, 1));
-    telemetry_kernel<<<grid, 256, 0, st>>>(t);
-    return cudaGetLastError();
+    return launch_kernel(telemetry_kernel, grid, dim3(256), 0, st, t);
 }
 
 template <typename K>
@@ -909,8 +905,7 @@ __global__ void pack_slopes_kernel(const BlockDev* __restrict__ blocks, const fl
 cudaError_t launch_pack_slopes(const BlockDev* blocks, int nblk, int max_cols, const float* s_pad, float* out,
                                cudaStream_t st) {
     const dim3 grid((max_cols + 255) / 256, nblk);
-    pack_slopes_kernel<<<grid, 256, 0, st>>>(blocks, s_pad, out);
-    return cudaGetLastError();
+    return launch_kernel(pack_slopes_kernel, grid, dim3(256), 0, st, blocks, s_pad, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -932,11 +927,16 @@ cudaError_t launch_relayout(int dtype, const void* src, int na, int ns, const Bl
     const long long per = (long long)na * max_pitch;
     const dim3 grid((unsigned)((per + 255) / 256 < 4096 ? (per + 255) / 256 : 4096), nblk);
     switch (dtype_size(dtype)) {
-        case 4: relayout_kernel<uint32_t><<<grid, 256, 0, st>>>((const uint32_t*)src, na, ns, blocks, (uint32_t*)dst); break;
-        case 2: relayout_kernel<uint16_t><<<grid, 256, 0, st>>>((const uint16_t*)src, na, ns, blocks, (uint16_t*)dst); break;
-        default: relayout_kernel<uint8_t><<<grid, 256, 0, st>>>((const uint8_t*)src, na, ns, blocks, (uint8_t*)dst); break;
+        case 4:
+            return launch_kernel(relayout_kernel<uint32_t>, grid, dim3(256), 0, st, (const uint32_t*)src, na, ns, blocks,
+                                 (uint32_t*)dst);
+        case 2:
+            return launch_kernel(relayout_kernel<uint16_t>, grid, dim3(256), 0, st, (const uint16_t*)src, na, ns, blocks,
+                                 (uint16_t*)dst);
+        default:
+            return launch_kernel(relayout_kernel<uint8_t>, grid, dim3(256), 0, st, (const uint8_t*)src, na, ns, blocks,
+                                 (uint8_t*)dst);
     }
-    return cudaGetLastError();
 }
 
 // One CTA per row: max |M_rj| (exact, order-free), the scale, then the codes.
@@ -972,8 +972,7 @@ __global__ void quantize_kernel(int dtype, int ns, const float* __restrict__ M, 
 cudaError_t launch_quantize(int dtype, int na, int ns, const float* M, size_t ld, void* codes, float* scale,
                             cudaStream_t st) {
     if (na <= 0) return cudaSuccess;
-    quantize_kernel<<<na, 256, 0, st>>>(dtype, ns, M, ld, codes, scale);
-    return cudaGetLastError();
+    return launch_kernel(quantize_kernel, dim3(na), dim3(256), 0, st, dtype, ns, M, ld, codes, scale);
 }
 
 __global__ void check_finite_kernel(const float* __restrict__ x, size_t n, int* bad) {
@@ -985,8 +984,7 @@ cudaError_t launch_check_finite(const float* x, size_t n, int* bad, cudaStream_t
     if (n == 0) return cudaSuccess;
     size_t g = (n + 255) / 256;
     if (g > 4096) g = 4096;
-    check_finite_kernel<<<(unsigned)g, 256, 0, st>>>(x, n, bad);
-    return cudaGetLastError();
+    return launch_kernel(check_finite_kernel, dim3((unsigned)g), dim3(256), 0, st, x, n, bad);
 }
 
 }  // namespace rtc

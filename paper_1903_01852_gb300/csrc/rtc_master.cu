@@ -230,10 +230,9 @@ int rtc_master_step(rtc_master* m, uint64_t frame_id) {
     if (m->stepped && frame_id <= m->last_id) return mfail(m, RTC_EORDER, "frame id not increasing");
     MCK(m, cudaSetDevice(m->dev));
     const int threads = 256;
-    master_kernel<<<(m->na + threads - 1) / threads, threads, 0, m->st>>>(
-        m->d_in, m->nshards, m->pitch, m->na, m->d_q, m->d_a, m->d_cmd, 1.0f - m->leak, m->gain, m->clip, m->amin,
-        m->amax);
-    MCK(m, cudaGetLastError());
+    MCK(m, launch_kernel(master_kernel, dim3((m->na + threads - 1) / threads), dim3(threads), 0, m->st,
+                         (const float*)m->d_in, m->nshards, m->pitch, m->na, (const float*)m->d_q, m->d_a, m->d_cmd,
+                         1.0f - m->leak, m->gain, m->clip, m->amin, m->amax));
     MCK(m, cudaMemcpyAsync(m->h_cmd, m->d_cmd, (size_t)m->na * 4, cudaMemcpyDeviceToHost, m->st));
     MCK(m, cudaEventRecord(m->ev_cmd, m->st));
     const int rc = polc(m);                // for the next frame, after the commands

@@ -160,10 +160,11 @@ extern "C" int rtc_reconstruct_noalloc(int32_t na, int32_t ns, const float* M, s
     float* part = scratch_address(&e);
     if (!part) return RTC_ECUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    split_gemv_kernel<<<dim3((na + kWarps - 1) / kWarps, nsplit), kWarps * 32, 0, st>>>(M, ld, na, ns, split_cols, s,
-                                                                                        part);
-    if (cudaGetLastError() != cudaSuccess) return RTC_ECUDA;
-    split_finalise_kernel<<<(na + 255) / 256, 256, 0, st>>>(part, nsplit, na, row_scale, q, a_in, a_out, 1.0f - leak,
-                                                             gain);
-    return cudaGetLastError() == cudaSuccess ? RTC_OK : RTC_ECUDA;
+    if (rtc::launch_kernel(split_gemv_kernel, dim3((na + kWarps - 1) / kWarps, nsplit), dim3(kWarps * 32), 0, st, M, ld, na,
+                      ns, split_cols, s, part) != cudaSuccess)
+        return RTC_ECUDA;
+    if (rtc::launch_kernel(split_finalise_kernel, dim3((na + 255) / 256), dim3(256), 0, st, (const float*)part, nsplit, na,
+                      row_scale, q, a_in, a_out, 1.0f - leak, gain) != cudaSuccess)
+        return RTC_ECUDA;
+    return RTC_OK;
 }

@@ -53,6 +53,7 @@ struct rtc_loop {
     bool has_polc = false, timing = false, telemetry = false, stage_timing = false;
     bool explicit_polc = false;     // s + D a formed before the reconstruction (RTC_POLC_EXPLICIT)
     bool partial = false;           // RTC_FLAG_PARTIAL: a shard, partial reconstruction only
+    int stream_priority = 0;        // CUDA priority of the loop and camera streams
     float** d_pout = nullptr;       // device word: where else the shard writes its partial
 
     // host plans
@@ -442,6 +443,7 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
     L->amax = P->amax;
     L->graphs = (G->flags & RTC_FLAG_GRAPHS) != 0;
     L->partial = (G->flags & RTC_FLAG_PARTIAL) != 0;
+    if (G->priority < 0) return fail(L, RTC_EINVAL, "priority must be >= 0");
     if (L->partial && (P->P || P->D || L->explicit_polc))
         return fail(L, RTC_EINVAL, "a RTC_FLAG_PARTIAL loop takes no POLC matrix (the master applies it)");
     if (G->tel_depth < 0 || G->tel_depth > (1 << 20)) return fail(L, RTC_EINVAL, "tel_depth must be in [0, 2^20]");
@@ -646,12 +648,16 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
                                        std::to_string(free_b) + " free");
 
     CK(L, configure_slopes(L->smem_bytes));
-    CK(L, cudaStreamCreateWithPriority(&L->st, cudaStreamNonBlocking, -5));   // clamped to the highest priority
+    // stream priority: the device's greatest, lowered by geometry->priority steps
+    int least = 0, greatest = 0;
+    CK(L, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    L->stream_priority = std::min(least, greatest + std::max(0, G->priority));
+    CK(L, cudaStreamCreateWithPriority(&L->st, cudaStreamNonBlocking, L->stream_priority));
     CK(L, cudaStreamCreateWithFlags(&L->st_tel, cudaStreamNonBlocking));
     L->st_w.assign(L->nwfs, nullptr);
     L->ev_w.assign(L->nwfs, nullptr);
     for (int k = 0; k < L->nwfs; ++k) {
-        CK(L, cudaStreamCreateWithPriority(&L->st_w[k], cudaStreamNonBlocking, -5));
+        CK(L, cudaStreamCreateWithPriority(&L->st_w[k], cudaStreamNonBlocking, L->stream_priority));
         CK(L, cudaEventCreateWithFlags(&L->ev_w[k], cudaEventDisableTiming));
     }
     CK(L, cudaEventCreateWithFlags(&L->ev_frame_end, cudaEventDisableTiming));
