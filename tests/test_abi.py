@@ -202,3 +202,11 @@ def test_partial_loops_and_master_validation_without_gpu(rtc):
     assert b"NaN" in rtc.lib.rtc_master_last_error(None)
     assert rtc.lib.rtc_master_step(None, 1) == rtc.RTC_EINVAL
     assert rtc.lib.rtc_master_destroy(None) == rtc.RTC_OK
+
+
+def test_negative_stream_priority_is_rejected_without_gpu(rtc):
+    from paper_1903_01852_gb300 import synth
+    cfg = synth.make_config("scao_small")
+    assert rtc.footprint(dict(cfg, priority=3))[0] > 0
+    with pytest.raises(rtc.RtcError, match="priority"):
+        rtc.footprint(dict(cfg, priority=-1))

@@ -218,3 +218,15 @@ def test_host_pixel_rows_beyond_the_in_flight_window(torch_cuda, tmp_path):
                        timeout=600, cwd=root)
     assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-3000:]
     assert r.stdout.startswith("ok")
+
+
+def test_lowest_stream_priority_gives_the_same_commands(rtc, torch_cuda):
+    # priority only orders the scheduling of CTAs among loops; a loop at a priority
+    # beyond the device's range (clamped to its lowest) computes the same bits
+    cfg = synth.make_config("scao_small", polc=True)
+    frames = synth.draw_frames(cfg, 3, seed=271)
+    with rtc.Loop(dict(cfg, priority=100)) as low, rtc.Loop(cfg) as high:
+        for k, f in enumerate(frames):
+            low.submit_frame(k + 1, f)
+            high.submit_frame(k + 1, f)
+            assert np.array_equal(low.get_commands(timeout_us=WAIT_US)[1], high.get_commands(timeout_us=WAIT_US)[1])
