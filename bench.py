@@ -266,11 +266,14 @@ def run_unpaced_timed(loop, dev_frames, steps, warmup, sampler, first_id):
     return rows, fid
 
 
-def run_host_path(loop, host_frames, plans, steps, warmup, sampler, first_id, paced, swap=None):
+def run_host_path(loop, host_frames, plans, steps, warmup, sampler, first_id, paced, swap=None, arrival=None):
     """Frames from page-locked host memory through rtc_submit_pixels (row chunks of all
     cameras interleaved) and rtc_get_commands.  Unpaced: latency = first submit -> commands
     returned.  Paced at the MCAO frame rate with the readout spread over the chunks:
-    latency = last chunk submitted (last pixel in) -> commands returned.
+    latency = last chunk submitted (last pixel in) -> commands returned; arrival (a list)
+    also gets, per timed frame, the time from the arrival of the last row chunk of every
+    camera (the start of the last round of submissions) -> commands returned, which
+    includes the host's submission of every camera's last chunk.
     swap = (seconds, kwargs): a background thread calls loop.update(**kwargs) every that
     many seconds during the timed frames (the paper's parameter-swap experiment); the
     frames that applied a swap are reported apart."""
@@ -300,12 +303,13 @@ def run_host_path(loop, host_frames, plans, steps, warmup, sampler, first_id, pa
             while time.perf_counter() < t_next:
                 pass
         t_first = time.perf_counter()
-        t_last = t_first
+        t_last = t_round = t_first
         for c in range(nch):
             if paced:
                 tc = t_next + c * dt
                 while time.perf_counter() < tc:
                     pass
+            t_round = time.perf_counter()
             for w, plan in enumerate(plans):
                 if c < len(plan):
                     r0, r1 = plan[c]
@@ -315,6 +319,8 @@ def run_host_path(loop, host_frames, plans, steps, warmup, sampler, first_id, pa
         t_done = time.perf_counter()
         if timed:
             lat.append(((t_done - t_last) if paced else (t_done - t_first)) * 1e6)
+            if arrival is not None:
+                arrival.append((t_done - t_round) * 1e6)
             if th is not None:
                 if k == warmup:
                     th.start()
@@ -578,6 +584,8 @@ def ours_arm(args, world, rank, local):
             # host-clock loops (paced and end-to-end): no CUDA events, whose records would add host
             # time before the launches that matter
             loops[name + "_host"] = rtc.Loop(cfgs[name], device=local, telemetry=True, updatable=(name == "f32"))
+        # the same FP32 loop with each LGS chunk's kernels enqueued before the chunk arrives
+        loops["f32_pre"] = rtc.Loop(cfg, device=local, telemetry=True, prelaunch=True)
         fid = 1
         # 1) timed region: K unpaced steps, frames resident in HBM (device events around the region)
         ms_total, ids, _, fid = run_unpaced(loops["f32"], dev_frames, args.steps, args.warmup, torch, sampler, fid)
@@ -594,10 +602,15 @@ def ours_arm(args, world, rank, local):
         pf_lat, fid = run_host_frames(loops["f32_host"], host_frames, args.steps, args.warmup, sampler, fid)
         # 3) camera-paced last-pixel latency (the paper's definition), FP32 and BF16
         paced = {}
-        for name in ("f32", "bf16"):
-            lat, fid = run_host_path(loops[name + "_host"], host_frames, plans, args.paced_frames, args.paced_warmup,
-                                     sampler, fid, paced=True)
+        for name, lp in (("f32", "f32_host"), ("bf16", "bf16_host"), ("f32_prelaunch", "f32_pre")):
+            arr = []
+            lat, fid = run_host_path(loops[lp], host_frames, plans, args.paced_frames, args.paced_warmup,
+                                     sampler, fid, paced=True, arrival=arr)
             paced[name] = stats(lat, 1e6 / PACED_HZ)
+            a = stats(arr, 1e6 / PACED_HZ)
+            paced[name]["from_arrival"] = {k: a[k] for k in ("p50", "p99", "p999", "jitter_rms", "deadline_misses")}
+        paced["f32_prelaunch"]["chunks"] = {k: loops["f32_pre"].info()["prelaunch_" + k]
+                                            for k in ("used", "cancelled", "expired")}
         # 4) the same paced FP32 loop while the whole control matrix is re-uploaded and swapped every second
         lat, fid, swap_info = run_host_path(loops["f32_host"], host_frames, plans, args.swap_frames,
                                             args.paced_warmup, sampler, fid, paced=True, swap=(1.0, {"M": cfg["M"]}))

@@ -54,6 +54,7 @@ extern "C" {
 #define RTC_EDROPPED  -5  /* chunk accepted, but the previous frame was incomplete and was dropped */
 #define RTC_ECUDA     -6  /* a CUDA runtime call failed; the loop should be destroyed */
 #define RTC_ENOENT    -7  /* the requested frame is no longer (or not yet) in the ring */
+#define RTC_ENOTSUP   -8  /* the device lacks a capability the request needs */
 
 /* ---- enumerations ---------------------------------------------------- */
 #define RTC_WFS_SH       0  /* Shack-Hartmann: centre of gravity per subaperture */
@@ -85,6 +86,10 @@ extern "C" {
 #define RTC_FLAG_PARTIAL   32u /* a shard of a loop split by WFS (rtc_master): the loop computes
                                   only its WFS's partial reconstruction and no control law;
                                   polc->P and polc->D must be NULL */
+#define RTC_FLAG_PRELAUNCH 64u /* pre-enqueue the kernels of each Shack-Hartmann row chunk when the
+                                  previous chunk of its WFS is submitted (see rtc_submit_pixels);
+                                  excludes RTC_FLAG_TIMING and RTC_FLAG_STAGE_TIMING; RTC_ENOTSUP on
+                                  a device without native atomics on host memory */
 
 #define RTC_MAX_WFS 16
 
@@ -148,6 +153,8 @@ typedef struct rtc_geometry {
                                     (clamped to the device's lowest); a loop with a shorter frame
                                     period given a higher priority gets the SMs first when frames
                                     of several loops are on the GPU together (rtc_server) */
+    int32_t prelaunch_wait_us;   /* RTC_FLAG_PRELAUNCH: how long pre-enqueued kernels wait for their
+                                    chunk before they give up, 0..1000000 (0 is taken as 10000) */
 } rtc_geometry;
 
 /* Pixel calibration (Section 2.2): c = (raw - dark) * flat, then the threshold.
@@ -254,7 +261,23 @@ typedef struct rtc_chunk {
  * rows, return RTC_EORDER and change nothing.
  * px from pageable memory may be reused when the call returns; px in
  * page-locked or device memory must stay unchanged until rtc_get_commands
- * has returned this frame. */
+ * has returned this frame.
+ * RTC_FLAG_PRELAUNCH (no counterpart in the paper, whose nodes launch work
+ * as pixels arrive): after a Shack-Hartmann chunk that leaves rows of its WFS
+ * to come, the call also enqueues the slope and MVM kernels of that WFS's next
+ * chunk as the previous frame had it (same rows, read in place), ahead of
+ * its arrival.  Their CTAs wait on a page-locked mailbox for at most
+ * geometry->prelaunch_wait_us; when the chunk arrives with those rows, in
+ * page-locked or device memory that can be read in place, the call only writes
+ * its address to the mailbox, so the GPU starts on it without a launch.
+ * Otherwise (other rows, pixels that must be copied, a dropped frame, the loop
+ * destroyed) the mailbox is cancelled and the kernels do nothing; if the wait
+ * ran out first, they gave up the same way.  Both cases fall back to ordinary
+ * launches, with the same results.  rtc_get_info counts the three outcomes.
+ * While kernels wait, anything that waits for all work on the device
+ * (cudaDeviceSynchronize, cudaFree, another loop's rtc_destroy) waits for them
+ * too: until their chunk arrives, the frame is dropped or the loop destroyed,
+ * or the wait runs out. */
 int rtc_submit_pixels(rtc_loop* loop, const rtc_chunk* chunk);
 
 /* Whole-frame entry point (Section 2.2's pixel handling for a whole frame at
@@ -434,6 +457,10 @@ typedef struct rtc_info {
     uint64_t device_bytes;     /* device memory held by the loop */
     uint64_t frames_done, frames_dropped, frames_overrun;
     uint64_t swaps;            /* parameter swaps applied (rtc_update) */
+    uint64_t prelaunch_used;       /* RTC_FLAG_PRELAUNCH: chunks whose pre-enqueued kernels ran them */
+    uint64_t prelaunch_cancelled;  /* ... whose arrival did not match them (other rows, pixels to copy)
+                                      or that were abandoned (frame dropped, loop destroyed) */
+    uint64_t prelaunch_expired;    /* ... whose kernels stopped waiting before the chunk arrived */
 } rtc_info;
 int rtc_get_info(rtc_loop* loop, rtc_info* out);
 

@@ -18,20 +18,20 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("RTC_LIBRARY") or os.path.join(HERE, "librtc.so")
 
 RTC_OK, RTC_EINVAL, RTC_ENOMEM, RTC_ETIMEDOUT = 0, -1, -2, -3
-RTC_EORDER, RTC_EDROPPED, RTC_ECUDA, RTC_ENOENT = -4, -5, -6, -7
+RTC_EORDER, RTC_EDROPPED, RTC_ECUDA, RTC_ENOENT, RTC_ENOTSUP = -4, -5, -6, -7, -8
 RTC_WFS_SH, RTC_WFS_PYRAMID = 0, 1
 RTC_F32, RTC_BF16, RTC_E4M3 = 0, 1, 2
 RTC_THRESH_SUBTRACT, RTC_THRESH_CLIP = 0, 1
 RTC_NORM_LOCAL, RTC_NORM_GLOBAL = 0, 1
 RTC_POLC_IMPLICIT, RTC_POLC_EXPLICIT = 0, 1
 RTC_FLAG_TIMING, RTC_FLAG_TELEMETRY, RTC_FLAG_STAGE_TIMING, RTC_FLAG_UPDATABLE, RTC_FLAG_GRAPHS = 1, 2, 4, 8, 16
-RTC_FLAG_PARTIAL = 32
+RTC_FLAG_PARTIAL, RTC_FLAG_PRELAUNCH = 32, 64
 RTC_MAX_WFS = 16
 RTC_TEL_SLOPES, RTC_TEL_COMMANDS, RTC_TEL_PARTIALS = 1, 2, 4
 DTYPES = {"f32": RTC_F32, "bf16": RTC_BF16, "e4m3": RTC_E4M3}
 CODE_NP = {RTC_F32: np.float32, RTC_BF16: np.uint16, RTC_E4M3: np.uint8}
 STATUS = {0: "RTC_OK", -1: "RTC_EINVAL", -2: "RTC_ENOMEM", -3: "RTC_ETIMEDOUT", -4: "RTC_EORDER",
-          -5: "RTC_EDROPPED", -6: "RTC_ECUDA", -7: "RTC_ENOENT"}
+          -5: "RTC_EDROPPED", -6: "RTC_ECUDA", -7: "RTC_ENOENT", -8: "RTC_ENOTSUP"}
 
 f32p = C.POINTER(C.c_float)
 
@@ -46,7 +46,7 @@ class rtc_wfs(C.Structure):
 class rtc_geometry(C.Structure):
     _fields_ = [("nwfs", C.c_int32), ("wfs", C.POINTER(rtc_wfs)), ("device", C.c_int32),
                 ("flags", C.c_uint32), ("ring", C.c_int32), ("tel_depth", C.c_int32), ("tel_streams", C.c_uint32),
-                ("tel_decimate", C.c_int32), ("priority", C.c_int32)]
+                ("tel_decimate", C.c_int32), ("priority", C.c_int32), ("prelaunch_wait_us", C.c_int32)]
 
 
 class rtc_calib(C.Structure):
@@ -104,7 +104,8 @@ class rtc_info(C.Structure):
                 ("nrows", C.c_int32), ("m_dtype", C.c_int32), ("p_dtype", C.c_int32),
                 ("m_bytes", C.c_uint64), ("p_bytes", C.c_uint64), ("pixel_bytes", C.c_uint64),
                 ("device_bytes", C.c_uint64), ("frames_done", C.c_uint64), ("frames_dropped", C.c_uint64),
-                ("frames_overrun", C.c_uint64), ("swaps", C.c_uint64)]
+                ("frames_overrun", C.c_uint64), ("swaps", C.c_uint64), ("prelaunch_used", C.c_uint64),
+                ("prelaunch_cancelled", C.c_uint64), ("prelaunch_expired", C.c_uint64)]
 
 
 class rtc_master_desc(C.Structure):
@@ -253,7 +254,7 @@ def describe(cfg, device=0, flags=0, ring=4, tel=(0, 0, 1)):
         darks[k] = _fptr(d)
         flats[k] = _fptr(f)
     st.geo = rtc_geometry(len(wl), warr, device, flags, ring, int(tel[0]), int(tel[1]), int(tel[2]),
-                          int(cfg.get("priority", 0)))
+                          int(cfg.get("priority", 0)), int(cfg.get("prelaunch_wait_us", 0)))
     ref = _f32(cfg.get("ref_slopes"))
     st.cal = rtc_calib(darks, flats, thr.ctypes.data_as(f32p), mode.ctypes.data_as(C.POINTER(C.c_int32)), _fptr(ref))
     mdt = DTYPES[cfg.get("M_dtype", "f32")]
@@ -294,14 +295,15 @@ class Loop:
 
     def __init__(self, cfg, device=0, timing=False, telemetry=False, ring=4, stage_timing=False, updatable=False,
                  graphs=False, tel_depth=0, tel_streams=RTC_TEL_SLOPES | RTC_TEL_COMMANDS, tel_decimate=1,
-                 partial=False, _handle=None):
+                 partial=False, prelaunch=False, _handle=None):
         self.cfg = cfg
         self.na = int(cfg["na"])
         self._owned = _handle is None
         if _handle is None:
             flags = ((RTC_FLAG_TIMING if timing or stage_timing else 0) | (RTC_FLAG_TELEMETRY if telemetry else 0)
                      | (RTC_FLAG_STAGE_TIMING if stage_timing else 0) | (RTC_FLAG_UPDATABLE if updatable else 0)
-                     | (RTC_FLAG_GRAPHS if graphs else 0) | (RTC_FLAG_PARTIAL if partial else 0))
+                     | (RTC_FLAG_GRAPHS if graphs else 0) | (RTC_FLAG_PARTIAL if partial else 0)
+                     | (RTC_FLAG_PRELAUNCH if prelaunch else 0))
             st = describe(cfg, device, flags, ring, (tel_depth, tel_streams, tel_decimate))
             h = C.c_void_p()
             _check(lib.rtc_create(C.byref(st.geo), C.byref(st.cal), C.byref(st.cm), C.byref(st.pol), C.byref(h)))

@@ -86,6 +86,31 @@ struct FinaliseArgs {
     float* const* pout;             // device word: where else a shard writes it (NULL: nowhere)
 };
 
+// Mailbox of a pre-enqueued row chunk, in page-locked host memory.  The host
+// writes px / pitch / row0 and then moves state from kChunkEmpty to kChunkFilled
+// (or kChunkCancelled) with one compare-and-swap; a one-warp gate kernel ahead of
+// the chunk's slope kernel waits a bounded time for a state other than
+// kChunkEmpty and, when the time is up, moves it to kChunkExpired with the same
+// compare-and-swap.  The first swap decides for both sides; the chunk's kernels
+// do their work only on kChunkFilled.
+enum : int { kChunkEmpty = 0, kChunkFilled = 1, kChunkCancelled = 2, kChunkExpired = 3 };
+struct alignas(16) ChunkDesc {
+    const uint16_t* px;       // device address of the chunk's first row
+    long long pitch;          // uint16 elements
+    int row0;                 // frame row of px
+    int state;                // kChunk*
+};
+static_assert(sizeof(ChunkDesc) == 32, "chunk mailbox layout");
+struct ChunkGate {
+    ChunkDesc* desc;          // device address of the mailbox
+    ChunkDesc* mirror;        // device memory: the settled mailbox, copied by the gate kernel for the
+                              // chunk's slope and MVM kernels (whose many CTAs then read the L2, not
+                              // one host cache line over the link)
+    int wfs;                  // the WFS whose pixels it addresses
+    unsigned max_polls;       // upper bound on the polls, whatever the clock says
+    unsigned long long limit_ns;   // how long the kernel waits for the host
+};
+
 // Frame pointers for one launch; pitch in uint16 elements.  px[w] holds pixel
 // row row0[w] of WFS w (row0 > 0 when only a chunk of the frame is addressed).
 struct FramePtrs {
@@ -161,7 +186,10 @@ cudaError_t launch_normalise(const int2* items, int item0, int nitems, int max_p
                              const WfsDev* wfs, const float* pscr, const float* ref, const float* pol, float* s_pad,
                              bool pdl, cudaStream_t st);
 
-// Slope kernel over the CTA table entries [cta0, cta0 + nctas).  The WFS table
+// Slope kernel over the CTA table entries [cta0, cta0 + nctas).  gate: a
+// pre-enqueued chunk; a one-warp kernel waits on the mailbox first, and the slope
+// kernel, its programmatic dependent, takes the pixel pointer of WFS gate->wfs
+// from the mailbox (and does nothing unless the host filled it).  The WFS table
 // (nwfs entries, host memory) travels in the kernel parameters.  host_px: the
 // variant that keeps all of a thread's pixel rows in flight, for small launches
 // that read pixels in place from page-locked host memory.  Each slope is
@@ -169,18 +197,20 @@ cudaError_t launch_normalise(const int2* items, int item0, int nitems, int max_p
 cudaError_t launch_slopes(const SlopeCta* ctas, int cta0, int nctas, const WfsDev* wfs, int nwfs,
                           const FramePtrs& fp, bool host_px, const uint16_t* xlist, const float* ref,
                           const float* pol, float* s_pad, float* pscr, unsigned* counters, int smem_bytes,
-                          cudaStream_t st);
+                          cudaStream_t st, const ChunkGate* gate = nullptr);
 
 // GEMV over blocks [b0, b0 + nb): out[b * out_stride + r] = sum_j M_b[r][j] x[x_off_b + j],
 // times out_scale[r] when out_scale is not NULL; with fin, the CTA completing the
 // last block of a row tile also finalises it (a, cmd) and the last tile sets the
 // completion word.  pdl: launched as a programmatic dependent of the previous
 // kernel in the stream (prefetches matrix tiles into L2, then waits for it);
-// avg_row_bytes sizes that prefetch.
+// avg_row_bytes sizes that prefetch.  gate_state: a pre-enqueued chunk's settled
+// mailbox state (device memory), read after that wait; the launch does nothing
+// unless it is kChunkFilled.
 cudaError_t launch_gemv(int dtype, const void* M, const BlockDev* blocks, int b0, int nb,
                         int na, const float* x, const float* out_scale, float* out,
                         long long out_stride, const FinaliseArgs* fin, long long avg_row_bytes,
-                        bool pdl, cudaStream_t st);
+                        bool pdl, cudaStream_t st, const int* gate_state = nullptr);
 
 // Telemetry: compact copy of the padded slope buffer, block by block.
 cudaError_t launch_pack_slopes(const BlockDev* blocks, int nblk, int max_cols,

@@ -357,16 +357,73 @@ struct SlopeArgs {
     float* s_pad;
     float* pscr;
     unsigned* counters;
+    ChunkGate gate;           // desc NULL: every pixel pointer is in fp
     FramePtrs fp;
     WfsDev wfs[kMaxWfs];
 };
 static_assert(sizeof(SlopeCta) == 48, "slope CTA entry is three 16-byte vectors");
 static_assert(sizeof(SlopeArgs) <= 4096, "slope kernel parameters");
 
-template <bool kAllRows>
+// The wait of a pre-enqueued chunk (one thread): polls the mailbox state
+// (system-scope acquire) with short sleeps until the host has moved it, at most
+// limit_ns by the global timer and max_polls polls; then claims it as expired
+// with a compare-and-swap, which fails if the host moved it in the meantime.
+// Returns the state that both sides act on.
+__device__ int chunk_gate_wait(const ChunkGate& g) {
+    int* st = &g.desc->state;
+    unsigned long long t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (unsigned poll = 0;; ++poll) {
+        int v;
+        asm volatile("ld.acquire.sys.global.b32 %0, [%1];" : "=r"(v) : "l"(st) : "memory");
+        if (v != kChunkEmpty) return v;
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (poll >= g.max_polls || t - t0 >= g.limit_ns) break;
+        __nanosleep(32);      // a read over the link takes about a microsecond anyway
+    }
+    int old;
+    asm volatile("atom.acq_rel.sys.global.cas.b32 %0, [%1], %2, %3;"
+                 : "=r"(old) : "l"(st), "r"(int(kChunkEmpty)), "r"(int(kChunkExpired)) : "memory");
+    return old == kChunkEmpty ? int(kChunkExpired) : old;
+}
+
+// One warp that holds a pre-enqueued chunk's place on its stream until the
+// mailbox is settled; the chunk's slope kernel, its programmatic dependent,
+// launches when it exits.  Waiting thus occupies one warp per camera, not the
+// slope kernel's CTAs (which would keep the other cameras' MVMs off the SMs).
+__global__ void __launch_bounds__(32) chunk_gate_kernel(const ChunkGate g) {
+    if (threadIdx.x != 0) return;
+    const int state = chunk_gate_wait(g);
+    if (state == kChunkFilled) {     // fields written before the host's swap
+        const volatile ChunkDesc* d = g.desc;
+        g.mirror->px = d->px;
+        g.mirror->pitch = d->pitch;
+        g.mirror->row0 = d->row0;
+    }
+    g.mirror->state = state;
+}
+
+template <bool kAllRows, bool kGated>
 __global__ void __launch_bounds__(kSlopeThreads) slopes_kernel(const __grid_constant__ SlopeArgs a) {
     extern __shared__ float sm[];
+    __shared__ ChunkDesc s_box;
+    if constexpr (kGated) {
+        pdl_wait();       // the gate kernel has ended: its mirror of the mailbox is written
+        if (threadIdx.x == 0) {
+            const ChunkDesc* d = a.gate.mirror;
+            s_box.state = __ldcg(&d->state);
+            if (s_box.state == kChunkFilled) {
+                s_box.px = reinterpret_cast<const uint16_t*>(__ldcg(reinterpret_cast<const long long*>(&d->px)));
+                s_box.pitch = __ldcg(&d->pitch);
+                s_box.row0 = __ldcg(&d->row0);
+            }
+        }
+        __syncthreads();
+    }
     pdl_trigger();        // the MVM may launch now and prefetch its matrix tiles while slopes run
+    if constexpr (kGated)
+        if (s_box.state != kChunkFilled) return;
     union {
         int4 v[3];
         SlopeCta c;
@@ -377,11 +434,21 @@ __global__ void __launch_bounds__(kSlopeThreads) slopes_kernel(const __grid_cons
     const SlopeRow& row = e.c.row;
     const int w = row.wfs;
     const WfsDev& W = a.wfs[w];
+    const uint16_t* px = a.fp.px[w];
+    long long pitch = a.fp.pitch[w];
+    int prow0 = a.fp.row0[w];
+    if constexpr (kGated) {
+        if (w == a.gate.wfs) {
+            px = s_box.px;
+            pitch = s_box.pitch;
+            prow0 = s_box.row0;
+        }
+    }
     if (W.kind == RTC_WFS_SH)
-        sh_part<kAllRows>(e.c.part, row, W, a.fp.px[w], a.fp.pitch[w], a.fp.row0[w], a.xlist, a.ref, a.pol, a.s_pad, a.pscr,
-                a.counters, sm);
+        sh_part<kAllRows>(e.c.part, row, W, px, pitch, prow0, a.xlist, a.ref, a.pol, a.s_pad, a.pscr,
+                                  a.counters, sm);
     else
-        pyr_row(row, W, a.fp.px[w], a.fp.pitch[w], a.fp.row0[w], a.xlist, a.ref, a.pol, a.s_pad, a.pscr);
+        pyr_row(row, W, px, pitch, prow0, a.xlist, a.ref, a.pol, a.s_pad, a.pscr);
 }
 
 // Global normalisation of pyramid slopes, a programmatic dependent of the slope
@@ -442,16 +509,18 @@ cudaError_t launch_normalise(const int2* items, int item0, int nitems, int max_p
 
 cudaError_t configure_slopes(int smem_bytes) {
     if (smem_bytes <= 48 * 1024) return cudaSuccess;
-    const cudaError_t e = cudaFuncSetAttribute(slopes_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               smem_bytes);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(slopes_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    for (auto k : {slopes_kernel<false, false>, slopes_kernel<true, false>, slopes_kernel<false, true>,
+                   slopes_kernel<true, true>}) {
+        const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_slopes(const SlopeCta* ctas, int cta0, int nctas, const WfsDev* wfs, int nwfs,
                           const FramePtrs& fp, bool host_px, const uint16_t* xlist, const float* ref,
                           const float* pol, float* s_pad, float* pscr, unsigned* counters, int smem_bytes,
-                          cudaStream_t st) {
+                          cudaStream_t st, const ChunkGate* gate) {
     if (nctas <= 0) return cudaSuccess;
     if (nwfs < 1 || nwfs > kMaxWfs) return cudaErrorInvalidValue;
     SlopeArgs a{};
@@ -465,8 +534,26 @@ cudaError_t launch_slopes(const SlopeCta* ctas, int cta0, int nctas, const WfsDe
     a.counters = counters;
     a.fp = fp;
     std::copy(wfs, wfs + nwfs, a.wfs);
-    if (host_px) return launch_kernel(slopes_kernel<true>, dim3(nctas), dim3(kSlopeThreads), smem_bytes, st, a);
-    return launch_kernel(slopes_kernel<false>, dim3(nctas), dim3(kSlopeThreads), smem_bytes, st, a);
+    const dim3 grid(nctas), block(kSlopeThreads);
+    if (gate) {
+        a.gate = *gate;
+        const cudaError_t e = launch_kernel(chunk_gate_kernel, dim3(1), dim3(32), 0, st, *gate);
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = grid;
+        cfg.blockDim = block;
+        cfg.dynamicSmemBytes = smem_bytes;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;     // launched at the gate kernel's exit, a few us before a stream-ordered launch
+        if (host_px) return cudaLaunchKernelEx(&cfg, slopes_kernel<true, true>, a);
+        return cudaLaunchKernelEx(&cfg, slopes_kernel<false, true>, a);
+    }
+    if (host_px) return launch_kernel(slopes_kernel<true, false>, grid, block, smem_bytes, st, a);
+    return launch_kernel(slopes_kernel<false, false>, grid, block, smem_bytes, st, a);
 }
 
 // ---------------------------------------------------------------------------
@@ -578,6 +665,7 @@ struct GemvArgs {
     long long out_stride;
     FinaliseArgs fin;
     int prefetch_ctas;         // CTAs [0, prefetch_ctas) prefetch their matrix tile into L2 before waiting
+    const int* gate_state;     // a pre-enqueued chunk's mailbox state: unless kChunkFilled, do nothing
 };
 
 #ifndef RTC_GEMV_F32_U
@@ -653,7 +741,9 @@ __device__ void finalise_tile(const FinaliseArgs& f, const float* __restrict__ p
     }
 }
 
-template <int DT, int U, int RI, int RPW>
+// kGated: a pre-enqueued chunk's MVM (the check of its mailbox costs the float32
+// variant two registers, so the other launches keep the kernels without it).
+template <int DT, int U, int RI, int RPW, bool kGated>
 __device__ __forceinline__ void gemv_body(const GemvArgs& a) {
     static_assert(RPW % RI == 0 && kFinRows % (kGemvWarps * RPW) == 0, "row tiling");
     __shared__ int s_last;
@@ -674,6 +764,8 @@ __device__ __forceinline__ void gemv_body(const GemvArgs& a) {
     }
     pdl_wait();           // the input vector (slopes or commands) is written by the previous kernel
     pdl_trigger();
+    if constexpr (kGated)     // written by the gate kernel, ahead of the slope kernel waited for above
+        if (__ldcg(a.gate_state) != kChunkFilled) return;
 #pragma unroll 1
     for (int rr = 0; rr < RPW; rr += RI) {
         const uint4* mrow[RI];
@@ -749,17 +841,17 @@ __device__ __forceinline__ void gemv_body(const GemvArgs& a) {
     }
 }
 
-template <int DT, int U, int RI, int RPW>
+template <int DT, int U, int RI, int RPW, bool kGated>
 __global__ void __launch_bounds__(kGemvWarps * 32) gemv_kernel(const __grid_constant__ GemvArgs a) {
-    gemv_body<DT, U, RI, RPW>(a);
+    gemv_body<DT, U, RI, RPW, kGated>(a);
 }
 
 // One row per warp: the launches over a single column block (the POLC product, a
 // row chunk's block) have about a thousand CTAs, and at <= 32 registers all of
 // them fit in one wave of eight CTAs per SM.
-template <int DT, int U, int RI>
+template <int DT, int U, int RI, bool kGated>
 __global__ void __launch_bounds__(kGemvWarps * 32, 8) gemv_kernel_1row(const __grid_constant__ GemvArgs a) {
-    gemv_body<DT, U, RI, RI>(a);
+    gemv_body<DT, U, RI, RI, kGated>(a);
 }
 
 // Telemetry entry of one frame: grid.y enumerates the recorded sections (one
@@ -856,7 +948,7 @@ cudaError_t launch_maybe_pdl(K kernel, dim3 grid, const GemvArgs& a, bool pdl, c
 #define RTC_GEMV_MIN_WAVES 2
 #endif
 
-template <int DT, int U, int RI>
+template <int DT, int U, int RI, bool kG>
 cudaError_t launch_gemv_t(const GemvArgs& base, int nb, long long avg_row_bytes, bool pdl, cudaStream_t st) {
     // rows per warp: as many as keep at least RTC_GEMV_MIN_WAVES waves of 8 CTAs per SM
     const int na = base.na;
@@ -874,23 +966,32 @@ cudaError_t launch_gemv_t(const GemvArgs& base, int nb, long long avg_row_bytes,
     // prefetch while waiting for the producer: about 96 MB, below the L2 size
     const long long tile_bytes = std::max(1LL, avg_row_bytes * kGemvWarps * rpw);
     a.prefetch_ctas = pdl ? (int)std::min<long long>(grid.x, (96LL << 20) / tile_bytes) : 0;
-    if (rpw >= 4) return launch_maybe_pdl(gemv_kernel<DT, U, RI, (RI > 4 ? RI : 4)>, grid, a, pdl, st);
+    if (rpw >= 4) return launch_maybe_pdl(gemv_kernel<DT, U, RI, (RI > 4 ? RI : 4), kG>, grid, a, pdl, st);
     if constexpr (!kNoRpw2)
-        if (rpw >= 2) return launch_maybe_pdl(gemv_kernel<DT, U, RI, (RI > 2 ? RI : 2)>, grid, a, pdl, st);
-    if constexpr (RI == 1) return launch_maybe_pdl(gemv_kernel_1row<DT, U, 1>, grid, a, pdl, st);
-    else return launch_maybe_pdl(gemv_kernel<DT, U, RI, RI>, grid, a, pdl, st);
+        if (rpw >= 2) return launch_maybe_pdl(gemv_kernel<DT, U, RI, (RI > 2 ? RI : 2), kG>, grid, a, pdl, st);
+    if constexpr (RI == 1) return launch_maybe_pdl(gemv_kernel_1row<DT, U, 1, kG>, grid, a, pdl, st);
+    else return launch_maybe_pdl(gemv_kernel<DT, U, RI, RI, kG>, grid, a, pdl, st);
 }
 
 cudaError_t launch_gemv(int dtype, const void* M, const BlockDev* blocks, int b0, int nb, int na, const float* x,
                         const float* out_scale, float* out, long long out_stride, const FinaliseArgs* fin,
-                        long long avg_row_bytes, bool pdl, cudaStream_t st) {
+                        long long avg_row_bytes, bool pdl, cudaStream_t st, const int* gate_state) {
     if (nb <= 0 || na <= 0) return cudaSuccess;
-    GemvArgs a{static_cast<const uint8_t*>(M), blocks, b0, 0, na, x, out_scale, out, out_stride, FinaliseArgs{}, 0};
+    GemvArgs a{static_cast<const uint8_t*>(M), blocks, b0, 0, na, x, out_scale, out, out_stride, FinaliseArgs{}, 0,
+               gate_state};
     if (fin) a.fin = *fin;
+    if (gate_state) {
+        switch (dtype) {
+            case RTC_F32: return launch_gemv_t<RTC_F32, RTC_GEMV_F32_U, RTC_GEMV_F32_RI, true>(a, nb, avg_row_bytes, pdl, st);
+            case RTC_BF16: return launch_gemv_t<RTC_BF16, RTC_GEMV_BF16_U, RTC_GEMV_BF16_RI, true>(a, nb, avg_row_bytes, pdl, st);
+            case RTC_E4M3: return launch_gemv_t<RTC_E4M3, RTC_GEMV_E4M3_U, RTC_GEMV_E4M3_RI, true>(a, nb, avg_row_bytes, pdl, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (dtype) {
-        case RTC_F32: return launch_gemv_t<RTC_F32, RTC_GEMV_F32_U, RTC_GEMV_F32_RI>(a, nb, avg_row_bytes, pdl, st);
-        case RTC_BF16: return launch_gemv_t<RTC_BF16, RTC_GEMV_BF16_U, RTC_GEMV_BF16_RI>(a, nb, avg_row_bytes, pdl, st);
-        case RTC_E4M3: return launch_gemv_t<RTC_E4M3, RTC_GEMV_E4M3_U, RTC_GEMV_E4M3_RI>(a, nb, avg_row_bytes, pdl, st);
+        case RTC_F32: return launch_gemv_t<RTC_F32, RTC_GEMV_F32_U, RTC_GEMV_F32_RI, false>(a, nb, avg_row_bytes, pdl, st);
+        case RTC_BF16: return launch_gemv_t<RTC_BF16, RTC_GEMV_BF16_U, RTC_GEMV_BF16_RI, false>(a, nb, avg_row_bytes, pdl, st);
+        case RTC_E4M3: return launch_gemv_t<RTC_E4M3, RTC_GEMV_E4M3_U, RTC_GEMV_E4M3_RI, false>(a, nb, avg_row_bytes, pdl, st);
         default: return cudaErrorInvalidValue;
     }
 }

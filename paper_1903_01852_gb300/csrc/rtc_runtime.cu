@@ -194,9 +194,35 @@ struct rtc_loop {
     std::vector<size_t> g_pitch;                 // [wfs] bytes
     std::vector<cudaGraphExec_t> g_exec;         // [slot]
     bool capturing = false;
+
+    // pre-enqueued row chunks (RTC_FLAG_PRELAUNCH)
+    bool prelaunch = false;
+    unsigned long long pre_limit_ns = 0;
+    unsigned pre_max_polls = 0;
+    ChunkDesc* h_box = nullptr;                  // page-locked mailboxes, kBoxesPerWfs per WFS
+    ChunkDesc* d_box = nullptr;                  // their device address
+    ChunkDesc* d_box_mirror = nullptr;           // device memory: each settled mailbox, for the kernels
+    std::vector<cudaEvent_t> ev_box;             // per mailbox: recorded after the kernels that read it
+    std::vector<int> box_next;                   // per WFS: the mailbox its next pre-enqueued chunk takes
+    struct PreChunk {
+        bool pending = false;                    // kernels enqueued, mailbox not yet settled
+        int row_begin = 0, row_end = 0;          // the rows they were enqueued for
+        int upto = 0, bu = 0;                    // slope rows and column blocks done after them
+        int box = 0;
+        bool host_px = false;
+    };
+    std::vector<PreChunk> pre;                   // per WFS
+    struct SeenChunk {
+        int row_begin, row_end;
+        bool in_place, host_px;
+    };
+    std::vector<std::vector<SeenChunk>> seen_prev, seen_cur;   // per WFS: chunks of the last two frames
+    uint64_t pre_used = 0, pre_cancelled = 0, pre_expired = 0;
 };
 
 namespace {
+
+constexpr int kBoxesPerWfs = 4;
 
 enum : unsigned { kUpdM = 1u, kUpdMscale = 2u, kUpdP = 4u, kUpdPscale = 8u, kUpdTable = 16u, kUpdRef = 32u };
 
@@ -286,6 +312,25 @@ void stop_stream(rtc_loop* L) {
     L->tel_streaming = false;
 }
 
+// Settles a pending pre-enqueued chunk's mailbox with `to` (kChunkFilled after
+// its fields were written, or kChunkCancelled).  Returns false if its kernels
+// had already stopped waiting (the mailbox expired; they do nothing).
+bool settle_prelaunched(rtc_loop* L, rtc_loop::PreChunk& p, int to) {
+    p.pending = false;
+    int expect = kChunkEmpty;
+    if (__atomic_compare_exchange_n(&L->h_box[p.box].state, &expect, to, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST))
+        return true;
+    ++L->pre_expired;
+    return false;
+}
+
+// Cancels every pending pre-enqueued chunk: its kernels end their wait and do
+// nothing (a frame dropped or abandoned, the loop destroyed).
+void cancel_prelaunched(rtc_loop* L) {
+    for (auto& p : L->pre)
+        if (p.pending && settle_prelaunched(L, p, kChunkCancelled)) ++L->pre_cancelled;
+}
+
 void release(rtc_loop* L) {
     if (!L) return;
     stop_stream(L);
@@ -296,6 +341,7 @@ void release(rtc_loop* L) {
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != L->dev) cudaSetDevice(L->dev);
+    cancel_prelaunched(L);                   // pre-enqueued kernels stop waiting
     if (L->st) cudaStreamSynchronize(L->st);
     if (L->st_tel) cudaStreamSynchronize(L->st_tel);
     for (cudaStream_t w : L->st_w)
@@ -304,6 +350,9 @@ void release(rtc_loop* L) {
         if (e) cudaEventDestroy(e);
     for (cudaStream_t w : L->st_w)
         if (w) cudaStreamDestroy(w);
+    for (cudaEvent_t e : L->ev_box)
+        if (e) cudaEventDestroy(e);
+    if (L->h_box) cudaFreeHost(L->h_box);
     if (L->ev_frame_end) cudaEventDestroy(L->ev_frame_end);
     for (auto& s : L->slots)
         for (cudaEvent_t e : {s.ev_start, s.ev_tail, s.ev_slopes, s.ev_mvm, s.ev_final, s.ev_polc, s.ev_tel})
@@ -456,6 +505,16 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
     if (L->graphs && L->updatable) return fail(L, RTC_EINVAL, "RTC_FLAG_GRAPHS and RTC_FLAG_UPDATABLE exclude each other");
     if (L->graphs && L->stage_timing)
         return fail(L, RTC_EINVAL, "RTC_FLAG_GRAPHS and RTC_FLAG_STAGE_TIMING exclude each other");
+    L->prelaunch = (G->flags & RTC_FLAG_PRELAUNCH) != 0;
+    if (G->prelaunch_wait_us < 0 || G->prelaunch_wait_us > 1000000)
+        return fail(L, RTC_EINVAL, "prelaunch_wait_us must be in [0, 1000000]");
+    if (L->prelaunch && L->timing)
+        return fail(L, RTC_EINVAL, "RTC_FLAG_PRELAUNCH excludes RTC_FLAG_TIMING and RTC_FLAG_STAGE_TIMING");
+    {
+        const unsigned long long wait_us = G->prelaunch_wait_us > 0 ? (unsigned long long)G->prelaunch_wait_us : 10000ull;
+        L->pre_limit_ns = wait_us * 1000ull;
+        L->pre_max_polls = (unsigned)(16 * wait_us + 64);   // a poll (a read over the link) takes longer than 1/16 us
+    }
 
     // ---- slope-row and block plans ------------------------------------
     const int V = elems_per_16B(L->m_dtype);
@@ -661,6 +720,25 @@ int create_impl(const rtc_geometry* G, const rtc_calib* C, const rtc_cmat* M, co
         CK(L, cudaEventCreateWithFlags(&L->ev_w[k], cudaEventDisableTiming));
     }
     CK(L, cudaEventCreateWithFlags(&L->ev_frame_end, cudaEventDisableTiming));
+    if (L->prelaunch) {
+        // the mailbox handshake is a compare-and-swap by both the CPU and the GPU on page-locked memory
+        int native = 0;
+        CK(L, cudaDeviceGetAttribute(&native, cudaDevAttrHostNativeAtomicSupported, L->dev));
+        if (!native) return fail(L, RTC_ENOTSUP, "RTC_FLAG_PRELAUNCH needs native GPU atomics on host memory");
+        const size_t nbox = (size_t)L->nwfs * kBoxesPerWfs;
+        CK(L, cudaHostAlloc(reinterpret_cast<void**>(&L->h_box), nbox * sizeof(ChunkDesc), cudaHostAllocMapped));
+        std::memset(static_cast<void*>(L->h_box), 0, nbox * sizeof(ChunkDesc));
+        void* dv = nullptr;
+        CK(L, cudaHostGetDevicePointer(&dv, L->h_box, 0));
+        L->d_box = static_cast<ChunkDesc*>(dv);
+        TRY(dev_alloc(L, &L->d_box_mirror, nbox * sizeof(ChunkDesc)));
+        L->ev_box.assign(nbox, nullptr);
+        for (cudaEvent_t& e : L->ev_box) CK(L, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        L->box_next.assign(L->nwfs, 0);
+        L->pre.assign(L->nwfs, rtc_loop::PreChunk{});
+        L->seen_prev.assign(L->nwfs, {});
+        L->seen_cur.assign(L->nwfs, {});
+    }
 
     // ---- device buffers ---------------------------------------------------
     TRY(dev_alloc(L, &L->d_blocks, L->blocks_h.size() * sizeof(BlockDev)));
@@ -959,6 +1037,13 @@ int begin_frame(rtc_loop* L, uint64_t id, bool chunked) {
     std::fill(L->rows_done.begin(), L->rows_done.end(), 0);
     std::fill(L->blks_done.begin(), L->blks_done.end(), 0);
     L->start_recorded = false;
+    if (L->prelaunch) {
+        cancel_prelaunched(L);     // none is pending between frames; kept as a guard
+        for (int k = 0; k < L->nwfs; ++k) {
+            L->seen_prev[k].swap(L->seen_cur[k]);
+            L->seen_cur[k].clear();
+        }
+    }
     return RTC_OK;
 }
 
@@ -1076,11 +1161,13 @@ FinaliseArgs fin_args(rtc_loop* L) {
 
 // host_px: the pixels are read in place from page-locked host memory (a row chunk):
 // the slope kernel variant with all of a thread's pixel rows in flight.
-int slopes_rows(rtc_loop* L, int r0, int r1, const FramePtrs& fp, bool host_px, cudaStream_t st) {
+// gate: a pre-enqueued chunk's mailbox (its CTAs wait on it for the pixel address).
+int slopes_rows(rtc_loop* L, int r0, int r1, const FramePtrs& fp, bool host_px, cudaStream_t st,
+                const ChunkGate* gate = nullptr) {
     const int p0 = L->part_start[r0], p1 = L->part_start[r1];
     const float* pol = L->explicit_polc ? L->d_u : nullptr;
     CK(L, launch_slopes(L->d_ctas, p0, p1 - p0, L->wfs_host.data(), L->nwfs, fp, host_px, L->d_xlist, L->d_ref, pol,
-                        L->d_s, L->d_pscr, L->d_row_cnt, L->smem_bytes, st));
+                        L->d_s, L->d_pscr, L->d_row_cnt, L->smem_bytes, st, gate));
     // globally normalised pyramids whose rows all ran here (they are never split across launches)
     int i0 = -1, i1 = -1;
     for (int k = 0; k < L->nwfs; ++k)
@@ -1101,6 +1188,7 @@ long long avg_row_bytes(const rtc_loop* L) {
 // A dropped frame may have counted some blocks of some row tiles: once all its
 // queued work is done, clear them; the next frame starts after that.
 int reset_counters(rtc_loop* L) {
+    cancel_prelaunched(L);
     TRY(join_wfs_streams(L));
     CK(L, cudaMemsetAsync(L->d_fin_cnt, 0, (size_t)L->nfin * sizeof(unsigned), L->st));
     CK(L, cudaEventRecord(L->ev_frame_end, L->st));
@@ -1129,6 +1217,64 @@ FramePtrs internal_frames(rtc_loop* L) {
         fp.pitch[k] = L->frame_pitch[k];
     }
     return fp;
+}
+
+// Enqueues, on WFS k's camera stream, the slope and MVM kernels of its next row
+// chunk as the previous frame had it (the chunk starting at the rows received so
+// far, read in place), waiting on a mailbox that rtc_submit_pixels fills when
+// that chunk arrives.  Nothing is enqueued when the previous frame had no such
+// chunk, when the chunk completes no slope row, or when the mailbox this WFS
+// takes next is still read by earlier kernels.
+int prelaunch_next(rtc_loop* L, int k) {
+    const rtc_wfs& w = L->wfs[k];
+    if (w.kind != RTC_WFS_SH) return RTC_OK;
+    const int rb = L->rows_in[k];
+    const rtc_loop::SeenChunk* e = nullptr;
+    for (const auto& x : L->seen_prev[k])
+        if (x.row_begin == rb) e = &x;
+    if (!e || !e->in_place) return RTC_OK;
+    const int r0 = L->wfs_row0[k];
+    const int done = L->rows_done[k];
+    int upto = done;
+    while (upto < L->wfs_nrows[k] && L->row_ready[r0 + upto] <= e->row_end) ++upto;
+    if (upto == done) return RTC_OK;
+    // the in-place conditions of submit_impl, for these rows
+    if (w.oy + done * w.npx < e->row_begin) return RTC_OK;
+    if (upto < w.nsuby && e->row_end > w.oy + upto * w.npx) return RTC_OK;
+    const int box = k * kBoxesPerWfs + L->box_next[k];
+    const cudaError_t q = cudaEventQuery(L->ev_box[box]);
+    if (q == cudaErrorNotReady) return RTC_OK;
+    CK(L, q);
+    L->box_next[k] = (L->box_next[k] + 1) % kBoxesPerWfs;
+    ChunkDesc& b = L->h_box[box];
+    b.px = nullptr;
+    b.pitch = 0;
+    b.row0 = 0;
+    __atomic_store_n(&b.state, (int)kChunkEmpty, __ATOMIC_SEQ_CST);   // before the launches below
+    const ChunkGate gate{L->d_box + box, L->d_box_mirror + box, k, L->pre_max_polls, L->pre_limit_ns};
+    FramePtrs fp = internal_frames(L);
+    fp.px[k] = nullptr;                        // from the mailbox
+    cudaStream_t sk = L->st_w[k];
+    const int b0 = L->wfs_blk0[k];
+    const int bd = L->blks_done[k];
+    int bu = bd;
+    while (bu < L->wfs_nblk[k] && L->blk_row_end[b0 + bu] <= upto) ++bu;
+    rtc_loop::PreChunk& p = L->pre[k];
+    p.row_begin = e->row_begin;
+    p.row_end = e->row_end;
+    p.upto = upto;
+    p.bu = bu;
+    p.box = box;
+    p.host_px = e->host_px;
+    TRY(slopes_rows(L, r0 + done, r0 + upto, fp, e->host_px, sk, &gate));
+    p.pending = true;                          // from here on every path settles the mailbox
+    if (bu > bd) {
+        const FinaliseArgs fa = fin_args(L);
+        CK(L, launch_gemv(L->m_dtype, L->d_M, L->d_blocks, b0 + bd, bu - bd, L->na, L->d_s, nullptr, L->d_part, L->na,
+                          &fa, avg_row_bytes(L), true, sk, &L->d_box_mirror[box].state));
+    }
+    CK(L, cudaEventRecord(L->ev_box[box], sk));
+    return RTC_OK;
 }
 
 int submit_impl(rtc_loop* L, const rtc_chunk* c) {
@@ -1195,27 +1341,55 @@ int submit_impl(rtc_loop* L, const rtc_chunk* c) {
             }
         }
     }
-    if (!in_place)
-        CK(L, cudaMemcpy2DAsync(L->d_frame[k] + (size_t)c->row_begin * L->frame_pitch[k], L->frame_pitch[k] * 2, c->px,
-                                c->pitch, (size_t)w.width * 2, c->row_end - c->row_begin, cudaMemcpyDefault, sk));
-    L->rows_in[k] = c->row_end;
-    const bool slopes_launched = upto > done;
-    if (slopes_launched) {
-        TRY(slopes_rows(L, r0 + done, r0 + upto, fp, in_place && host_px, sk));
-        L->rows_done[k] = upto;
+    if (L->prelaunch) L->seen_cur[k].push_back({c->row_begin, c->row_end, in_place, host_px});
+    // the kernels of this chunk may have been enqueued already, waiting on a mailbox
+    bool taken = false;
+    if (L->prelaunch && L->pre[k].pending) {
+        rtc_loop::PreChunk& p = L->pre[k];
+        const bool match = in_place && host_px == p.host_px && c->row_begin == p.row_begin &&
+                           c->row_end == p.row_end && upto == p.upto;
+        if (match) {
+            ChunkDesc& b = L->h_box[p.box];
+            b.px = fp.px[k];
+            b.pitch = fp.pitch[k];
+            b.row0 = fp.row0[k];
+        }
+        if (settle_prelaunched(L, p, match ? kChunkFilled : kChunkCancelled)) {
+            taken = match;
+            if (!match) ++L->pre_cancelled;
+        }
+        if (taken) {
+            ++L->pre_used;
+            L->rows_in[k] = c->row_end;
+            L->rows_done[k] = upto;
+            L->blks_done[k] = p.bu;
+        }
     }
-    if (last && L->stage_timing) CK(L, cudaEventRecord(s.ev_slopes, sk));
-    // column blocks completed by those slope rows
-    const int b0 = L->wfs_blk0[k];
-    int bd = L->blks_done[k];
-    int bu = bd;
-    while (bu < L->wfs_nblk[k] && L->blk_row_end[b0 + bu] <= L->rows_done[k]) ++bu;
-    if (bu > bd) {
-        const FinaliseArgs fa = fin_args(L);
-        CK(L, launch_gemv(L->m_dtype, L->d_M, L->d_blocks, b0 + bd, bu - bd, L->na, L->d_s, nullptr, L->d_part, L->na,
-                          &fa, avg_row_bytes(L), slopes_launched && !L->stage_timing, sk));
-        L->blks_done[k] = bu;
+    if (!taken) {
+        if (!in_place)
+            CK(L, cudaMemcpy2DAsync(L->d_frame[k] + (size_t)c->row_begin * L->frame_pitch[k], L->frame_pitch[k] * 2,
+                                    c->px, c->pitch, (size_t)w.width * 2, c->row_end - c->row_begin, cudaMemcpyDefault,
+                                    sk));
+        L->rows_in[k] = c->row_end;
+        const bool slopes_launched = upto > done;
+        if (slopes_launched) {
+            TRY(slopes_rows(L, r0 + done, r0 + upto, fp, in_place && host_px, sk));
+            L->rows_done[k] = upto;
+        }
+        if (last && L->stage_timing) CK(L, cudaEventRecord(s.ev_slopes, sk));
+        // column blocks completed by those slope rows
+        const int b0 = L->wfs_blk0[k];
+        int bd = L->blks_done[k];
+        int bu = bd;
+        while (bu < L->wfs_nblk[k] && L->blk_row_end[b0 + bu] <= L->rows_done[k]) ++bu;
+        if (bu > bd) {
+            const FinaliseArgs fa = fin_args(L);
+            CK(L, launch_gemv(L->m_dtype, L->d_M, L->d_blocks, b0 + bd, bu - bd, L->na, L->d_s, nullptr, L->d_part,
+                              L->na, &fa, avg_row_bytes(L), slopes_launched && !L->stage_timing, sk));
+            L->blks_done[k] = bu;
+        }
     }
+    if (L->prelaunch && !last && L->rows_in[k] < w.height) TRY(prelaunch_next(L, k));
     if (last) {
         if (L->stage_timing) CK(L, cudaEventRecord(s.ev_mvm, sk));
         TRY(join_wfs_streams(L));              // POLC and telemetry follow every camera's work
@@ -1910,6 +2084,9 @@ int rtc_get_info(rtc_loop* L, rtc_info* out) {
     out->frames_dropped = L->frames_dropped;
     out->frames_overrun = L->frames_overrun;
     out->swaps = L->swaps;
+    out->prelaunch_used = L->pre_used;
+    out->prelaunch_cancelled = L->pre_cancelled;
+    out->prelaunch_expired = L->pre_expired;
     return RTC_OK;
 }
 

@@ -210,3 +210,17 @@ def test_negative_stream_priority_is_rejected_without_gpu(rtc):
     assert rtc.footprint(dict(cfg, priority=3))[0] > 0
     with pytest.raises(rtc.RtcError, match="priority"):
         rtc.footprint(dict(cfg, priority=-1))
+
+
+def test_prelaunch_flag_validation_without_gpu(rtc):
+    from paper_1903_01852_gb300 import synth
+    cfg = synth.make_config("scao_small")
+    pre = rtc.RTC_FLAG_PRELAUNCH
+    assert rtc.footprint(cfg, flags=pre)[0] > 0
+    assert rtc.footprint(dict(cfg, prelaunch_wait_us=1_000_000), flags=pre)[0] > 0
+    for timing in (rtc.RTC_FLAG_TIMING, rtc.RTC_FLAG_STAGE_TIMING):
+        with pytest.raises(rtc.RtcError, match="PRELAUNCH excludes"):
+            rtc.footprint(cfg, flags=pre | timing)      # events would be recorded out of order
+    for bad in (-1, 1_000_001):
+        with pytest.raises(rtc.RtcError, match="prelaunch_wait_us"):
+            rtc.footprint(dict(cfg, prelaunch_wait_us=bad), flags=pre)

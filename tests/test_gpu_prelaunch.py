@@ -1,0 +1,198 @@
+"""Pre-enqueued row chunks (RTC_FLAG_PRELAUNCH) through the C ABI: the kernels of
+a Shack-Hartmann chunk enqueued ahead of its arrival, waiting on a page-locked
+mailbox.  They give the same bits as ordinary launches and match the FP64
+oracle; a chunk that does not match the prediction, pixels that must be
+copied, a wait that runs out and an abandoned frame all fall back to ordinary
+launches, and the loop's counters say which happened."""
+import time
+
+import numpy as np
+import pytest
+
+from oracle import OracleLoop
+from paper_1903_01852_gb300 import synth
+from parity_util import TOL_F32, WAIT_US, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    assert torch.cuda.is_available()
+    return torch
+
+
+def sh_loop(seed=501, fmt="f32"):
+    """Three SH cameras of different shapes (subaperture rows of 6 to 10 pixels)
+    and one pyramid, which is never pre-enqueued."""
+    rng = np.random.default_rng(seed)
+    wfs = [synth.sh_wfs(rng, 12, 8, 104, 100, 0.2, nblocks=4),
+           synth.sh_wfs(rng, 9, 10, 96, 94, 0.0, nblocks=3),
+           synth.sh_wfs(rng, 16, 6, 100, 99, 0.0, nblocks=4),
+           synth.pyramid_wfs(rng, 10, 26, 24, 0.0, nblocks=2)]
+    ns = sum(2 * synth.num_valid(w) for w in wfs)
+    na = 157
+    cfg = dict(name="prelaunch", na=na, ns=ns, wfs=wfs, M=synth.control_matrix(rng, na, ns, sd=1e-2), M_scale=None,
+               M_dtype="f32", P=synth.polc_matrix(rng, na), P_scale=None, P_dtype="f32", gain=0.4, leak=0.02,
+               clip=None, a0=rng.normal(0, 0.05, na).astype(np.float32),
+               ref_slopes=rng.normal(0, 0.1, ns).astype(np.float32))
+    if fmt != "f32":
+        from oracle import quantize_rows
+        codes, scale = quantize_rows(cfg["M"], fmt)
+        pc, ps = quantize_rows(cfg["P"], fmt)
+        cfg.update(M=codes, M_scale=scale, M_dtype=fmt, P=pc, P_scale=ps, P_dtype=fmt)
+    return cfg
+
+
+def in_place_buffers(torch, frames, where):
+    """Each frame's WFS images in page-locked host ("host") or device memory, rows
+    16-byte aligned with a pitch that is a multiple of 16 bytes, so that chunks are
+    read in place."""
+    out = []
+    for f in frames:
+        bufs = []
+        for x in f:
+            h, wd = x.shape
+            wp = (wd + 7) // 8 * 8
+            src = torch.from_numpy(np.ascontiguousarray(x).view(np.int16))
+            if where == "host":
+                t = torch.zeros((h, wp), dtype=torch.int16, pin_memory=True)
+            else:
+                t = torch.zeros((h, wp), dtype=torch.int16, device="cuda")
+            t[:, :wd] = src.to(t.device)
+            bufs.append(t[:, :wd])
+        out.append(bufs)
+    return out
+
+
+def submit(loop, fid, bufs, plans, upto=None):
+    """Chunks of all cameras interleaved (chunk c of every WFS, then c + 1); upto
+    stops after that many chunk rounds."""
+    n = max(len(p) for p in plans)
+    for c in range(n if upto is None else upto):
+        for w, plan in enumerate(plans):
+            if c < len(plan):
+                r0, r1 = plan[c]
+                loop.submit(fid, w, r0, r1, bufs[w][r0:r1])
+
+
+def expected_prelaunches(cfg, plans, frames_after_first):
+    return frames_after_first * sum(len(p) - 1 for w, p in zip(cfg["wfs"], plans) if w["kind"] == "sh")
+
+
+@pytest.mark.parametrize("where,fmt", [("host", "f32"), ("device", "f32"), ("host", "bf16"), ("host", "e4m3")])
+def test_prelaunched_chunks_match_ordinary_launches_and_the_oracle(rtc, torch_cuda, where, fmt):
+    cfg = sh_loop(fmt=fmt)
+    frames = synth.draw_frames(cfg, 5, seed=502)
+    plans = [synth.chunk_plan(w, 4) for w in cfg["wfs"]]
+    bufs = in_place_buffers(torch_cuda, frames, where)
+    ref = OracleLoop(cfg)
+    with rtc.Loop(cfg, telemetry=True, prelaunch=True) as pre, rtc.Loop(cfg, telemetry=True) as plain:
+        for k, f in enumerate(frames):
+            submit(pre, k + 1, bufs[k], plans)
+            submit(plain, k + 1, bufs[k], plans)
+            (fa, a), (fb, b) = pre.get_commands(timeout_us=WAIT_US), plain.get_commands(timeout_us=WAIT_US)
+            sa, sb = pre.get_telemetry(fa, timeout_us=WAIT_US)[0], plain.get_telemetry(fb, timeout_us=WAIT_US)[0]
+            assert fa == fb == k + 1
+            assert np.array_equal(a, b) and np.array_equal(sa, sb)
+            s_ref, a_ref = ref.step(f)
+            assert rel(sa, s_ref) <= TOL_F32 and rel(a, a_ref) <= TOL_F32
+        info = pre.info()
+        assert info["prelaunch_used"] == expected_prelaunches(cfg, plans, len(frames) - 1)
+        assert info["prelaunch_cancelled"] == 0 and info["prelaunch_expired"] == 0
+        assert plain.info()["prelaunch_used"] == 0
+        assert pre.check_guards() == 0
+
+
+def test_other_chunk_rows_and_pageable_pixels_cancel_the_prediction(rtc, torch_cuda):
+    cfg = sh_loop(seed=511)
+    frames = synth.draw_frames(cfg, 6, seed=512)
+    four = [synth.chunk_plan(w, 4) for w in cfg["wfs"]]
+    three = [synth.chunk_plan(w, 3) for w in cfg["wfs"]]
+    bufs = in_place_buffers(torch_cuda, frames, "host")
+    # frames 1-2 four chunks; 3 three chunks (predictions from 2 miss); 4 three chunks
+    # (predicted right); 5 four chunks from pageable memory (must be copied); 6 four chunks
+    sched = [(four, True), (four, True), (three, True), (three, True), (four, False), (four, True)]
+    ref = OracleLoop(cfg)
+    with rtc.Loop(cfg, prelaunch=True) as pre, rtc.Loop(cfg) as plain:
+        for k, (f, (plans, pinned)) in enumerate(zip(frames, sched)):
+            src = bufs[k] if pinned else [np.ascontiguousarray(x) for x in f]
+            submit(pre, k + 1, src, plans)
+            submit(plain, k + 1, src, plans)
+            a, b = pre.get_commands(timeout_us=WAIT_US)[1], plain.get_commands(timeout_us=WAIT_US)[1]
+            assert np.array_equal(a, b)
+            assert rel(a, ref.step(f)[1]) <= TOL_F32
+        info = pre.info()
+        assert info["prelaunch_cancelled"] > 0 and info["prelaunch_expired"] == 0
+        n4 = expected_prelaunches(cfg, four, 1)
+        n3 = expected_prelaunches(cfg, three, 1)
+        # used: every chunk after the first of frame 2 (predicted from 1) and of frame 4
+        # (from 3); in frame 3 the chunks that frame 2 also had (a boundary both plans
+        # share); none in frame 5 (copied) nor 6 (its predictions come from frame 5)
+        shared = sum(1 for w, p3, p4 in zip(cfg["wfs"], three, four) if w["kind"] == "sh"
+                     for c in range(1, len(p3)) if p3[c] in p4)
+        assert info["prelaunch_used"] == n4 + n3 + shared
+        assert pre.check_guards() == 0
+
+
+def test_a_wait_that_runs_out_falls_back_to_ordinary_launches(rtc, torch_cuda):
+    # the pre-enqueued kernels give up after 2 ms; the chunk arrives 50 ms later
+    cfg = dict(sh_loop(seed=521), prelaunch_wait_us=2000)
+    frames = synth.draw_frames(cfg, 3, seed=522)
+    plans = [synth.chunk_plan(w, 4) for w in cfg["wfs"]]
+    bufs = in_place_buffers(torch_cuda, frames, "host")
+    ref = OracleLoop(cfg)
+    with rtc.Loop(cfg, prelaunch=True) as pre, rtc.Loop(cfg) as plain:
+        for k, f in enumerate(frames):
+            if k == 1:
+                submit(pre, k + 1, bufs[k], plans, upto=1)
+                time.sleep(0.05)
+                n = max(len(p) for p in plans)
+                for c in range(1, n):
+                    for w, plan in enumerate(plans):
+                        if c < len(plan):
+                            pre.submit(k + 1, w, *plan[c], bufs[k][w][plan[c][0]:plan[c][1]])
+            else:
+                submit(pre, k + 1, bufs[k], plans)
+            submit(plain, k + 1, bufs[k], plans)
+            a, b = pre.get_commands(timeout_us=WAIT_US)[1], plain.get_commands(timeout_us=WAIT_US)[1]
+            assert np.array_equal(a, b)
+            assert rel(a, ref.step(f)[1]) <= TOL_F32
+        info = pre.info()
+        nsh = sum(1 for w in cfg["wfs"] if w["kind"] == "sh")
+        assert info["prelaunch_expired"] == nsh               # chunk 1 of every SH camera in frame 2
+        assert info["prelaunch_used"] == expected_prelaunches(cfg, plans, 2) - nsh
+
+
+def test_an_abandoned_frame_cancels_its_pending_kernels(rtc, torch_cuda):
+    # waits of up to 1 s: the drop and the destroy below come first and cancel them
+    cfg = dict(sh_loop(seed=531), prelaunch_wait_us=1_000_000)
+    frames = synth.draw_frames(cfg, 4, seed=532)
+    plans = [synth.chunk_plan(w, 4) for w in cfg["wfs"]]
+    bufs = in_place_buffers(torch_cuda, frames, "host")
+    with rtc.Loop(cfg, prelaunch=True) as pre, rtc.Loop(cfg) as plain:
+        for lp in (pre, plain):
+            submit(lp, 1, bufs[0], plans)
+            lp.get_commands(timeout_us=WAIT_US)
+            submit(lp, 2, bufs[1], plans, upto=2)            # frame 2 never completes
+        with pytest.raises(TimeoutError):                     # its pixels are not all in
+            pre.get_commands(timeout_us=100_000)
+        for lp in (pre, plain):
+            assert lp.submit(3, 0, *plans[0][0], bufs[2][0][plans[0][0][0]:plans[0][0][1]]) == rtc.RTC_EDROPPED
+            for c in range(max(len(p) for p in plans)):
+                for w, plan in enumerate(plans):
+                    if c < len(plan) and (c, w) != (0, 0):
+                        lp.submit(3, w, *plan[c], bufs[2][w][plan[c][0]:plan[c][1]])
+        a, b = pre.get_commands(timeout_us=WAIT_US), plain.get_commands(timeout_us=WAIT_US)
+        assert a[0] == b[0] == 3 and np.array_equal(a[1], b[1])
+        info = pre.info()
+        nsh = sum(1 for w in cfg["wfs"] if w["kind"] == "sh")
+        assert info["frames_dropped"] == 1 and info["prelaunch_cancelled"] == nsh
+        # frame 4 goes half way; destroying the loop cancels what waits for the rest (before
+        # the other loop is destroyed: its cudaFree waits for all work on the device)
+        submit(pre, 4, bufs[3], plans, upto=2)
+        assert pre.info()["prelaunch_expired"] == 0
+        t0 = time.perf_counter()
+        pre.close()
+        assert time.perf_counter() - t0 < 0.5

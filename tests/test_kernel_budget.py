@@ -16,17 +16,25 @@ SRC = os.path.join(ROOT, "paper_1903_01852_gb300", "csrc", "rtc_kernels.cu")
 
 # mangled entry -> (what, register budget, spill budget in bytes)
 BUDGET = {
-    "_ZN3rtc11gemv_kernelILi0ELi4ELi1ELi4EEEvNS_8GemvArgsE": ("float32 MVM, 4 rows per warp", 32, 0),
+    "_ZN3rtc11gemv_kernelILi0ELi4ELi1ELi4ELb0EEEvNS_8GemvArgsE": ("float32 MVM, 4 rows per warp", 32, 0),
     # one row per warp (single-block launches: the POLC product, a row chunk's block, and every
     # float32 launch too small for four rows per warp): held to 32 registers so that their ~1000
     # CTAs fit one wave (no spill with packed float32 sums; a few bytes allowed)
-    "_ZN3rtc16gemv_kernel_1rowILi0ELi4ELi1EEEvNS_8GemvArgsE": ("float32 MVM, 1 row per warp", 32, 32),
-    "_ZN3rtc11gemv_kernelILi1ELi2ELi4ELi4EEEvNS_8GemvArgsE": ("BF16 MVM", 64, 0),
-    "_ZN3rtc11gemv_kernelILi2ELi1ELi4ELi4EEEvNS_8GemvArgsE": ("E4M3 MVM", 48, 0),
-    "_ZN3rtc13slopes_kernelILb0EEEvNS_9SlopeArgsE": ("slope kernel", 64, 0),
+    "_ZN3rtc16gemv_kernel_1rowILi0ELi4ELi1ELb0EEEvNS_8GemvArgsE": ("float32 MVM, 1 row per warp", 32, 32),
+    "_ZN3rtc11gemv_kernelILi1ELi2ELi4ELi4ELb0EEEvNS_8GemvArgsE": ("BF16 MVM", 64, 0),
+    "_ZN3rtc11gemv_kernelILi2ELi1ELi4ELi4ELb0EEEvNS_8GemvArgsE": ("E4M3 MVM", 48, 0),
+    # a pre-enqueued chunk's MVM (its mailbox checked after the wait for the slopes); a chunk's
+    # launches are small enough to take one row per warp
+    "_ZN3rtc16gemv_kernel_1rowILi0ELi4ELi1ELb1EEEvNS_8GemvArgsE": ("float32 MVM, 1 row per warp, pre-enqueued",
+                                                                  32, 32),
+    "_ZN3rtc13slopes_kernelILb0ELb0EEEvNS_9SlopeArgsE": ("slope kernel", 64, 0),
     # pixels read over the CPU-GPU link: every pixel row of a thread in flight at once (launched for
     # row chunks and page-locked frames, where a few CTAs per SM are enough)
-    "_ZN3rtc13slopes_kernelILb1EEEvNS_9SlopeArgsE": ("slope kernel, host pixels", 168, 0),
+    "_ZN3rtc13slopes_kernelILb1ELb0EEEvNS_9SlopeArgsE": ("slope kernel, host pixels", 168, 0),
+    # pre-enqueued chunks (launched behind the one-warp gate kernel); the host-pixel one is compiled to
+    # 128 registers with a word or two spilled
+    "_ZN3rtc13slopes_kernelILb0ELb1EEEvNS_9SlopeArgsE": ("slope kernel, pre-enqueued", 64, 0),
+    "_ZN3rtc13slopes_kernelILb1ELb1EEEvNS_9SlopeArgsE": ("slope kernel, host pixels, pre-enqueued", 168, 16),
 }
 
 
