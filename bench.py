@@ -267,10 +267,10 @@ def run_unpaced_timed(loop, dev_frames, steps, warmup, sampler, first_id):
 
 
 def run_host_path(loop, host_frames, plans, steps, warmup, sampler, first_id, paced, swap=None, arrival=None):
-    """Frames from page-locked host memory through rtc_submit_pixels (row chunks of all
-    cameras interleaved) and rtc_get_commands.  Unpaced: latency = first submit -> commands
-    returned.  Paced at the MCAO frame rate with the readout spread over the chunks:
-    latency = last chunk submitted (last pixel in) -> commands returned; arrival (a list)
+    """Frames from page-locked host memory through rtc_submit_pixels_n (each round of row
+    chunks, chunk c of every camera, in one call) and rtc_get_commands.  Unpaced: latency =
+    first submit -> commands returned.  Paced at the MCAO frame rate with the readout spread
+    over the chunks: latency = last round submitted (last pixel in) -> commands returned; arrival (a list)
     also gets, per timed frame, the time from the arrival of the last row chunk of every
     camera (the start of the last round of submissions) -> commands returned, which
     includes the host's submission of every camera's last chunk.
@@ -292,6 +292,7 @@ def run_host_path(loop, host_frames, plans, steps, warmup, sampler, first_id, pa
     dt = READOUT_MS * 1e-3 / nch
     lat = []
     fid = first_id
+    rounds = {}     # (frame buffer, round) -> its chunk array; only the frame ids change
     gc.disable()
     t_next = time.perf_counter() + 0.002
     for k in range(warmup + steps):
@@ -310,11 +311,14 @@ def run_host_path(loop, host_frames, plans, steps, warmup, sampler, first_id, pa
                 while time.perf_counter() < tc:
                     pass
             t_round = time.perf_counter()
-            for w, plan in enumerate(plans):
-                if c < len(plan):
-                    r0, r1 = plan[c]
-                    t_last = time.perf_counter()
-                    loop.submit(fid, w, r0, r1, f[w][r0:r1])
+            arr = rounds.get((k % len(host_frames), c))
+            if arr is None:
+                arr = loop.chunks(fid, [(w, *p[c], f[w][p[c][0]:p[c][1]]) for w, p in enumerate(plans) if c < len(p)])
+                rounds[(k % len(host_frames), c)] = arr
+            for ch in arr:
+                ch.frame_id = fid
+            t_last = time.perf_counter()
+            loop.submit_chunks(arr)
         loop.get_commands(timeout_us=10_000_000)
         t_done = time.perf_counter()
         if timed:
@@ -584,8 +588,9 @@ def ours_arm(args, world, rank, local):
             # host-clock loops (paced and end-to-end): no CUDA events, whose records would add host
             # time before the launches that matter
             loops[name + "_host"] = rtc.Loop(cfgs[name], device=local, telemetry=True, updatable=(name == "f32"))
-        # the same FP32 loop with each LGS chunk's kernels enqueued before the chunk arrives
-        loops["f32_pre"] = rtc.Loop(cfg, device=local, telemetry=True, prelaunch=True)
+        # the same loops with each LGS chunk's kernels enqueued before the chunk arrives
+        for name in ("f32", "bf16"):
+            loops[name + "_pre"] = rtc.Loop(cfgs[name], device=local, telemetry=True, prelaunch=True)
         fid = 1
         # 1) timed region: K unpaced steps, frames resident in HBM (device events around the region)
         ms_total, ids, _, fid = run_unpaced(loops["f32"], dev_frames, args.steps, args.warmup, torch, sampler, fid)
@@ -602,15 +607,17 @@ def ours_arm(args, world, rank, local):
         pf_lat, fid = run_host_frames(loops["f32_host"], host_frames, args.steps, args.warmup, sampler, fid)
         # 3) camera-paced last-pixel latency (the paper's definition), FP32 and BF16
         paced = {}
-        for name, lp in (("f32", "f32_host"), ("bf16", "bf16_host"), ("f32_prelaunch", "f32_pre")):
+        for name, lp in (("f32", "f32_host"), ("bf16", "bf16_host"), ("f32_prelaunch", "f32_pre"),
+                         ("bf16_prelaunch", "bf16_pre")):
             arr = []
             lat, fid = run_host_path(loops[lp], host_frames, plans, args.paced_frames, args.paced_warmup,
                                      sampler, fid, paced=True, arrival=arr)
             paced[name] = stats(lat, 1e6 / PACED_HZ)
             a = stats(arr, 1e6 / PACED_HZ)
             paced[name]["from_arrival"] = {k: a[k] for k in ("p50", "p99", "p999", "jitter_rms", "deadline_misses")}
-        paced["f32_prelaunch"]["chunks"] = {k: loops["f32_pre"].info()["prelaunch_" + k]
-                                            for k in ("used", "cancelled", "expired")}
+        for name in ("f32", "bf16"):
+            paced[name + "_prelaunch"]["chunks"] = {k: loops[name + "_pre"].info()["prelaunch_" + k]
+                                                    for k in ("used", "cancelled", "expired")}
         # 4) the same paced FP32 loop while the whole control matrix is re-uploaded and swapped every second
         lat, fid, swap_info = run_host_path(loops["f32_host"], host_frames, plans, args.swap_frames,
                                             args.paced_warmup, sampler, fid, paced=True, swap=(1.0, {"M": cfg["M"]}))

@@ -280,6 +280,14 @@ typedef struct rtc_chunk {
  * or the wait runs out. */
 int rtc_submit_pixels(rtc_loop* loop, const rtc_chunk* chunk);
 
+/* Several chunks in one call (no counterpart in the paper; for a host that
+ * receives the rows of several cameras at once): the same as calling
+ * rtc_submit_pixels on chunks[0], ..., chunks[n-1] in that order.  Stops at
+ * the first chunk that fails and returns its status; *accepted (may be NULL)
+ * receives the number of chunks accepted before it.  Returns RTC_EDROPPED if
+ * any accepted chunk dropped a frame, else RTC_OK.  n = 0 does nothing. */
+int rtc_submit_pixels_n(rtc_loop* loop, const rtc_chunk* chunks, int32_t n, int32_t* accepted);
+
 /* Whole-frame entry point (Section 2.2's pixel handling for a whole frame at
  * once), for frames in device memory (e.g. written there by a frame grabber)
  * or in page-locked host memory (read over the CPU-GPU link): px[w] points at

@@ -118,6 +118,7 @@ SIGNATURES = [
                              C.POINTER(rtc_polc), C.POINTER(C.c_void_p)]),
     ("rtc_destroy", C.c_int, [C.c_void_p]),
     ("rtc_submit_pixels", C.c_int, [C.c_void_p, C.POINTER(rtc_chunk)]),
+    ("rtc_submit_pixels_n", C.c_int, [C.c_void_p, C.POINTER(rtc_chunk), C.c_int32, C.POINTER(C.c_int32)]),
     ("rtc_process_frame", C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(C.c_void_p), C.POINTER(C.c_size_t)]),
     ("rtc_next_frame_buffers", C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_size_t)]),
     ("rtc_submit_frame_graph", C.c_int, [C.c_void_p, C.c_uint64]),
@@ -338,6 +339,21 @@ class Loop:
         whose first row is row_begin.  Returns RTC_OK or RTC_EDROPPED."""
         ch = rtc_chunk(frame_id, wfs, row_begin, row_end, _ptr(px), _pitch(px) if pitch is None else pitch)
         return _check(lib.rtc_submit_pixels(self._h, C.byref(ch)), self._h, allow=(RTC_EDROPPED,))
+
+    @staticmethod
+    def chunks(frame_id, items):
+        """A ctypes array of rtc_chunk for submit_chunks: items are (wfs, row_begin, row_end, px)
+        with px as for submit.  Its frame_id fields may be rewritten for later frames."""
+        arr = (rtc_chunk * len(items))()
+        for i, (w, r0, r1, px) in enumerate(items):
+            arr[i] = rtc_chunk(frame_id, w, r0, r1, _ptr(px), _pitch(px))
+        return arr
+
+    def submit_chunks(self, arr):
+        """rtc_submit_pixels_n on a ctypes array of rtc_chunk (see chunks).  Returns RTC_OK
+        or RTC_EDROPPED; raises on the first chunk that fails (those before it are accepted)."""
+        acc = C.c_int32()
+        return _check(lib.rtc_submit_pixels_n(self._h, arr, len(arr), C.byref(acc)), self._h, allow=(RTC_EDROPPED,))
 
     def submit_frame(self, frame_id, frames, plans=None):
         """Submit a whole frame as row chunks; ``plans[w]`` lists (row_begin, row_end) for WFS w

@@ -1627,6 +1627,22 @@ int rtc_submit_pixels(rtc_loop* L, const rtc_chunk* chunk) {
     return submit_impl(L, chunk);
 }
 
+int rtc_submit_pixels_n(rtc_loop* L, const rtc_chunk* chunks, int32_t n, int32_t* accepted) {
+    if (accepted) *accepted = 0;
+    if (!L) return fail(nullptr, RTC_EINVAL, "loop is NULL");
+    if (n < 0 || (n > 0 && !chunks)) return fail(L, RTC_EINVAL, "n must be >= 0 and chunks non-NULL");
+    if (L->broken) return fail(L, RTC_ECUDA, "loop is in a failed state: " + L->err);
+    TRY(use_device(L));
+    int status = RTC_OK;
+    for (int32_t i = 0; i < n; ++i) {
+        const int rc = submit_impl(L, chunks + i);
+        if (rc != RTC_OK && rc != RTC_EDROPPED) return rc;
+        if (rc == RTC_EDROPPED) status = rc;
+        if (accepted) *accepted = i + 1;
+    }
+    return status;
+}
+
 int rtc_process_frame(rtc_loop* L, uint64_t frame_id, const uint16_t* const* px, const size_t* pitch) {
     if (!L) return fail(nullptr, RTC_EINVAL, "loop is NULL");
     if (L->broken) return fail(L, RTC_ECUDA, "loop is in a failed state: " + L->err);

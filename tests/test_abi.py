@@ -224,3 +224,9 @@ def test_prelaunch_flag_validation_without_gpu(rtc):
     for bad in (-1, 1_000_001):
         with pytest.raises(rtc.RtcError, match="prelaunch_wait_us"):
             rtc.footprint(dict(cfg, prelaunch_wait_us=bad), flags=pre)
+
+
+def test_batched_submission_validation_without_gpu(rtc):
+    acc = C.c_int32(7)
+    assert rtc.lib.rtc_submit_pixels_n(None, None, 0, C.byref(acc)) == rtc.RTC_EINVAL
+    assert acc.value == 0                                     # zeroed whatever the outcome

@@ -196,3 +196,46 @@ def test_an_abandoned_frame_cancels_its_pending_kernels(rtc, torch_cuda):
         t0 = time.perf_counter()
         pre.close()
         assert time.perf_counter() - t0 < 0.5
+
+
+@pytest.mark.parametrize("prelaunch", [False, True])
+def test_batched_rounds_equal_chunk_by_chunk_submission(rtc, torch_cuda, prelaunch):
+    # rtc_submit_pixels_n: one call per round of chunks (chunk c of every camera)
+    cfg = sh_loop(seed=541)
+    frames = synth.draw_frames(cfg, 4, seed=542)
+    plans = [synth.chunk_plan(w, 4) for w in cfg["wfs"]]
+    bufs = in_place_buffers(torch_cuda, frames, "host")
+    n = max(len(p) for p in plans)
+    with rtc.Loop(cfg, prelaunch=prelaunch) as batched, rtc.Loop(cfg) as single:
+        for k in range(len(frames)):
+            for c in range(n):
+                items = [(w, *p[c], bufs[k][w][p[c][0]:p[c][1]]) for w, p in enumerate(plans) if c < len(p)]
+                assert batched.submit_chunks(batched.chunks(k + 1, items)) == rtc.RTC_OK
+            submit(single, k + 1, bufs[k], plans)
+            a, b = batched.get_commands(timeout_us=WAIT_US), single.get_commands(timeout_us=WAIT_US)
+            assert a[0] == b[0] == k + 1 and np.array_equal(a[1], b[1])
+        if prelaunch:
+            assert batched.info()["prelaunch_used"] == expected_prelaunches(cfg, plans, len(frames) - 1)
+
+
+def test_a_batch_stops_at_its_first_bad_chunk(rtc, torch_cuda):
+    import ctypes as C
+    cfg = sh_loop(seed=551)
+    frames = synth.draw_frames(cfg, 1, seed=552)
+    plans = [synth.chunk_plan(w, 2) for w in cfg["wfs"]]
+    bufs = in_place_buffers(torch_cuda, frames, "host")[0]
+    with rtc.Loop(cfg) as lp:
+        # WFS 0 chunk 0, WFS 0 chunk 0 again (rows out of order), WFS 1 chunk 0
+        items = [(0, *plans[0][0], bufs[0][plans[0][0][0]:plans[0][0][1]]),
+                 (0, *plans[0][0], bufs[0][plans[0][0][0]:plans[0][0][1]]),
+                 (1, *plans[1][0], bufs[1][plans[1][0][0]:plans[1][0][1]])]
+        arr = lp.chunks(1, items)
+        acc = C.c_int32(-1)
+        assert rtc.lib.rtc_submit_pixels_n(lp._h, arr, 3, C.byref(acc)) == rtc.RTC_EORDER
+        assert acc.value == 1
+        # the rest of the frame, then its commands are complete and correct
+        rest = [(w, *p[c], bufs[w][p[c][0]:p[c][1]]) for c in range(2) for w, p in enumerate(plans)
+                if c < len(p) and (w, c) != (0, 0)]
+        assert lp.submit_chunks(lp.chunks(1, rest)) == rtc.RTC_OK
+        fid, a = lp.get_commands(timeout_us=WAIT_US)
+        assert fid == 1 and rel(a, OracleLoop(cfg).step(frames[0])[1]) <= TOL_F32
