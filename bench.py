@@ -921,8 +921,8 @@ def variants_arm(args):
         del exp_cfg
         out["polc"] = {"definition": "polc_product_us: the POLC kernel after the command (stage timing, "
                                      "serialised); unpaced_frame_period_us: back-to-back frames from HBM; "
-                                     "paced_latency_us: last pixel in -> commands returned at "
-                                     f"{PACED_HZ:.0f} Hz", **polc}
+                                     "paced_latency_us: last pixel in (the last round's one rtc_submit_pixels_n "
+                                     f"call) -> commands returned at {PACED_HZ:.0f} Hz", **polc}
         # (2) telemetry streaming
         tel = {}
         all_streams = rtc.RTC_TEL_SLOPES | rtc.RTC_TEL_COMMANDS | rtc.RTC_TEL_PARTIALS
@@ -938,7 +938,8 @@ def variants_arm(args):
             tel["with"] = stats(lat, 1e6 / PACED_HZ)
             tel["stream"] = st
             tel["entry_bytes"] = st["bytes"] // max(st["entries"], 1)
-        out["telemetry"] = {"definition": "paced MCAO FP32, last pixel in -> commands returned; 'with': every "
+        out["telemetry"] = {"definition": "paced MCAO FP32, last pixel in (the last round's one submission "
+                                          "call) -> commands returned; 'with': every "
                                           "frame's slopes, commands and 9 per-WFS partial command vectors written "
                                           "by the GPU into a 1000-entry page-locked circular buffer, drained by the "
                                           "library's stream thread (copy out of the buffer, write() to /dev/null)",
@@ -952,13 +953,20 @@ def variants_arm(args):
                     continue
                 c = dict(base, wfs=[dict(w, nblocks=nch) if w["nsubx"] > 2 else w for w in base["wfs"]])
                 pl = [synth.chunk_plan(w, nch if w["nsubx"] > 2 else 1) for w in c["wfs"]]
-                with rtc.Loop(c) as lp:
-                    lat, _ = run_host_path(lp, host, pl, n_paced, n_warm, sampler, 1, paced=True)
-                chunks[f"{nch}_{fmt}"] = stats(lat, 1e6 / PACED_HZ)
+                for pre in (False, True):
+                    arr = []
+                    with rtc.Loop(c, prelaunch=pre) as lp:
+                        lat, _ = run_host_path(lp, host, pl, n_paced, n_warm, sampler, 1, paced=True, arrival=arr)
+                    a = stats(arr, 1e6 / PACED_HZ)
+                    chunks[f"{nch}_{fmt}{'_prelaunch' if pre else ''}"] = {
+                        **{k: a[k] for k in ("p50", "p99", "p999", "jitter_rms", "deadline_misses", "n")},
+                        "last_submission_p50": stats(lat)["p50"]}
         del bcfg
-        out["chunks"] = {"definition": "paced MCAO latency (last pixel in -> commands returned, 500 Hz, 1.6 ms "
-                                       "readout) with each LGS camera's frame in N row chunks and its slopes in N "
-                                       "column blocks; key N_format", **chunks}
+        out["chunks"] = {"definition": "paced MCAO latency (arrival of every camera's last rows -> commands "
+                                       "returned, 500 Hz, 1.6 ms readout, one rtc_submit_pixels_n call per round) "
+                                       "with each LGS camera's frame in N row chunks and its slopes in N column "
+                                       "blocks, with and without RTC_FLAG_PRELAUNCH; key N_format[_prelaunch]",
+                         **chunks}
         del cfg, frames, dev, host
         torch.cuda.empty_cache()
         # (4) pyramid normalisation
