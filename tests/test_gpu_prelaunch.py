@@ -239,3 +239,44 @@ def test_a_batch_stops_at_its_first_bad_chunk(rtc, torch_cuda):
         assert lp.submit_chunks(lp.chunks(1, rest)) == rtc.RTC_OK
         fid, a = lp.get_commands(timeout_us=WAIT_US)
         assert fid == 1 and rel(a, OracleLoop(cfg).step(frames[0])[1]) <= TOL_F32
+
+
+def test_prelaunch_across_a_parameter_swap(rtc, torch_cuda):
+    # the swap applies at a frame boundary, where no pre-enqueued chunk is pending
+    from oracle import stored_matrix
+    cfg = sh_loop(seed=561)
+    rng = np.random.default_rng(562)
+    M2 = synth.control_matrix(rng, cfg["na"], cfg["ns"], sd=1e-2)
+    frames = synth.draw_frames(cfg, 6, seed=563)
+    plans = [synth.chunk_plan(w, 4) for w in cfg["wfs"]]
+    bufs = in_place_buffers(torch_cuda, frames, "host")
+    ref = OracleLoop(cfg)
+    with rtc.Loop(cfg, updatable=True, prelaunch=True) as pre, rtc.Loop(cfg, updatable=True) as plain:
+        for k, f in enumerate(frames):
+            if k == 3:
+                for lp in (pre, plain):
+                    lp.update(M=M2, control=(0.3, 0.05, None))
+                ref.cfg = dict(cfg, M=M2, gain=0.3, leak=0.05)
+                ref.m = stored_matrix(M2, "f32", None)
+            submit(pre, k + 1, bufs[k], plans)
+            submit(plain, k + 1, bufs[k], plans)
+            a, b = pre.get_commands(timeout_us=WAIT_US)[1], plain.get_commands(timeout_us=WAIT_US)[1]
+            assert np.array_equal(a, b)
+            assert rel(a, ref.step(f)[1]) <= TOL_F32
+        assert pre.info()["swaps"] == 1
+        assert pre.info()["prelaunch_used"] == expected_prelaunches(cfg, plans, len(frames) - 1)
+
+
+def test_prelaunch_in_a_shard_loop(rtc, torch_cuda):
+    # a RTC_FLAG_PARTIAL loop (one WFS group of a split loop): its partial reconstruction
+    cfg = dict(sh_loop(seed=571), P=None, P_scale=None)
+    frames = synth.draw_frames(cfg, 4, seed=572)
+    plans = [synth.chunk_plan(w, 4) for w in cfg["wfs"]]
+    bufs = in_place_buffers(torch_cuda, frames, "host")
+    with rtc.Loop(cfg, partial=True, prelaunch=True) as pre, rtc.Loop(cfg, partial=True) as plain:
+        for k in range(len(frames)):
+            submit(pre, k + 1, bufs[k], plans)
+            submit(plain, k + 1, bufs[k], plans)
+            a, b = pre.get_commands(timeout_us=WAIT_US)[1], plain.get_commands(timeout_us=WAIT_US)[1]
+            assert np.array_equal(a, b)
+        assert pre.info()["prelaunch_used"] == expected_prelaunches(cfg, plans, len(frames) - 1)
