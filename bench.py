@@ -266,14 +266,17 @@ def run_unpaced_timed(loop, dev_frames, steps, warmup, sampler, first_id):
     return rows, fid
 
 
-def run_host_path(loop, host_frames, plans, steps, warmup, sampler, first_id, paced, swap=None, arrival=None):
+def run_host_path(loop, host_frames, plans, steps, warmup, sampler, first_id, paced, swap=None, arrival=None,
+                  slowest=None):
     """Frames from page-locked host memory through rtc_submit_pixels_n (each round of row
     chunks, chunk c of every camera, in one call) and rtc_get_commands.  Unpaced: latency =
     first submit -> commands returned.  Paced at the MCAO frame rate with the readout spread
     over the chunks: latency = last round submitted (last pixel in) -> commands returned; arrival (a list)
     also gets, per timed frame, the time from the arrival of the last row chunk of every
     camera (the start of the last round of submissions) -> commands returned, which
-    includes the host's submission of every camera's last chunk.
+    includes the host's submission of every camera's last chunk.  slowest (a dict) receives
+    the slowest timed frame's split: its index, the time spent in the submission calls of
+    the frame, and the time rtc_get_commands waited.
     swap = (seconds, kwargs): a background thread calls loop.update(**kwargs) every that
     many seconds during the timed frames (the paper's parameter-swap experiment); the
     frames that applied a swap are reported apart."""
@@ -305,6 +308,7 @@ def run_host_path(loop, host_frames, plans, steps, warmup, sampler, first_id, pa
                 pass
         t_first = time.perf_counter()
         t_last = t_round = t_first
+        in_calls = 0.0
         for c in range(nch):
             if paced:
                 tc = t_next + c * dt
@@ -319,10 +323,15 @@ def run_host_path(loop, host_frames, plans, steps, warmup, sampler, first_id, pa
                 ch.frame_id = fid
             t_last = time.perf_counter()
             loop.submit_chunks(arr)
+            in_calls += time.perf_counter() - t_last
+        t_wait = time.perf_counter()
         loop.get_commands(timeout_us=10_000_000)
         t_done = time.perf_counter()
         if timed:
             lat.append(((t_done - t_last) if paced else (t_done - t_first)) * 1e6)
+            if slowest is not None and lat[-1] > slowest.get("latency_us", -1.0):
+                slowest.update(frame=k - warmup, latency_us=lat[-1], submit_calls_us=in_calls * 1e6,
+                               get_commands_wait_us=(t_done - t_wait) * 1e6)
             if arrival is not None:
                 arrival.append((t_done - t_round) * 1e6)
             if th is not None:
@@ -609,10 +618,11 @@ def ours_arm(args, world, rank, local):
         paced = {}
         for name, lp in (("f32", "f32_host"), ("bf16", "bf16_host"), ("f32_prelaunch", "f32_pre"),
                          ("bf16_prelaunch", "bf16_pre")):
-            arr = []
+            arr, slow = [], {}
             lat, fid = run_host_path(loops[lp], host_frames, plans, args.paced_frames, args.paced_warmup,
-                                     sampler, fid, paced=True, arrival=arr)
+                                     sampler, fid, paced=True, arrival=arr, slowest=slow)
             paced[name] = stats(lat, 1e6 / PACED_HZ)
+            paced[name]["slowest_frame"] = {k: (round(v, 1) if isinstance(v, float) else v) for k, v in slow.items()}
             a = stats(arr, 1e6 / PACED_HZ)
             paced[name]["from_arrival"] = {k: a[k] for k in ("p50", "p99", "p999", "jitter_rms", "deadline_misses")}
         for name in ("f32", "bf16"):
