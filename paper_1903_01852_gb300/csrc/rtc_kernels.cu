@@ -579,6 +579,25 @@ __device__ __forceinline__ uint4 ld_stream(const uint4* p) {
 __device__ __forceinline__ float bf_lo(uint32_t u) { return __uint_as_float(u << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
 
+#ifndef RTC_GEMV_GROUP_MIN_WAVES
+#define RTC_GEMV_GROUP_MIN_WAVES 2 // waves of 8 CTAs per SM a grouped launch keeps at least
+#endif
+// Consecutive column blocks one MVM CTA takes (its row tile of each, one fused
+// finalisation for all), per storage format.  BF16 and E4M3 rows of a block are
+// short (about 2.2 and 1.1 KB on MCAO), so a one-block CTA spends much of its
+// life on its fixed costs; two blocks per CTA: MCAO BF16 MVM 138.9 -> 132.7 us,
+// E4M3 108.1 -> 99.9 us, LTAO BF16 85.6 -> 75.4 us.  Float32 rows are long
+// enough (one block: 243.2 us, two: 245.3 us).
+#ifndef RTC_GEMV_GROUP_F32
+#define RTC_GEMV_GROUP_F32 1
+#endif
+#ifndef RTC_GEMV_GROUP_BF16
+#define RTC_GEMV_GROUP_BF16 2
+#endif
+#ifndef RTC_GEMV_GROUP_E4M3
+#define RTC_GEMV_GROUP_E4M3 2
+#endif
+
 #ifndef RTC_GEMV_FFMA2_MASK
 #define RTC_GEMV_FFMA2_MASK 1      // storage formats (bit 1 << dtype) that sum with packed FMAs: float32
 #endif
@@ -657,6 +676,7 @@ struct GemvArgs {
     const uint8_t* M;
     const BlockDev* blocks;
     int b0;
+    int nb;                    // column blocks of the launch: b0 .. b0 + nb - 1
     int tiles;                 // row tiles per block
     int na;
     const float* x;
@@ -666,6 +686,7 @@ struct GemvArgs {
     FinaliseArgs fin;
     int prefetch_ctas;         // CTAs [0, prefetch_ctas) prefetch their matrix tile into L2 before waiting
     const int* gate_state;     // a pre-enqueued chunk's mailbox state: unless kChunkFilled, do nothing
+    int group;                 // column blocks per CTA (consecutive, same row tile), >= 1
 };
 
 #ifndef RTC_GEMV_F32_U
@@ -743,29 +764,38 @@ __device__ void finalise_tile(const FinaliseArgs& f, const float* __restrict__ p
 
 // kGated: a pre-enqueued chunk's MVM (the check of its mailbox costs the float32
 // variant two registers, so the other launches keep the kernels without it).
-template <int DT, int U, int RI, int RPW, bool kGated>
+// kGroup: consecutive column blocks per CTA (1: one block, the loop compiles away).
+template <int DT, int U, int RI, int RPW, bool kGated, int kGroup>
 __device__ __forceinline__ void gemv_body(const GemvArgs& a) {
     static_assert(RPW % RI == 0 && kFinRows % (kGemvWarps * RPW) == 0, "row tiling");
     __shared__ int s_last;
-    const int bi = blockIdx.x / a.tiles;
-    const int tile = blockIdx.x - bi * a.tiles;
-    const int b = a.b0 + bi;
-    const BlockDev B = a.blocks[b];
+    const int bg = blockIdx.x / a.tiles;
+    const int tile = blockIdx.x - bg * a.tiles;
+    const int g0 = bg * kGroup;                          // the CTA's blocks: [g0, g1) of the launch
+    const int g1 = kGroup == 1 ? g0 + 1 : min(g0 + kGroup, a.nb);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nvec = B.pitch / Elem<DT>::kPer16;
-    const float* x = a.x + B.x_off;
     constexpr size_t esz = 16 / Elem<DT>::kPer16;
     const int r0 = tile * kGemvWarps * RPW;
     const int rbase = r0 + warp * RPW;
+    BlockDev B = a.blocks[a.b0 + g0];                    // the first block's entry, before the wait
     if (threadIdx.x == 0 && (int)blockIdx.x < a.prefetch_ctas && r0 < a.na) {
         const int rows = min(r0 + kGemvWarps * RPW, a.na) - r0;
-        const unsigned bytes = (unsigned)((size_t)rows * B.pitch * esz);
-        if (bytes) prefetch_l2(a.M + (size_t)(B.m_off + (long long)r0 * B.pitch) * esz, bytes);
+        for (int g = g0; g < g1; ++g) {
+            const BlockDev Bg = g == g0 ? B : a.blocks[a.b0 + g];
+            const unsigned bytes = (unsigned)((size_t)rows * Bg.pitch * esz);
+            if (bytes) prefetch_l2(a.M + (size_t)(Bg.m_off + (long long)r0 * Bg.pitch) * esz, bytes);
+        }
     }
     pdl_wait();           // the input vector (slopes or commands) is written by the previous kernel
     pdl_trigger();
     if constexpr (kGated)     // written by the gate kernel, ahead of the slope kernel waited for above
         if (__ldcg(a.gate_state) != kChunkFilled) return;
+#pragma unroll 1
+    for (int g = g0; g < g1; ++g) {
+    const int b = a.b0 + g;
+    if (g != g0) B = a.blocks[b];
+    const int nvec = B.pitch / Elem<DT>::kPer16;
+    const float* x = a.x + B.x_off;
 #pragma unroll 1
     for (int rr = 0; rr < RPW; rr += RI) {
         const uint4* mrow[RI];
@@ -804,6 +834,7 @@ __device__ __forceinline__ void gemv_body(const GemvArgs& a) {
             if (lane == 0 && ok[i]) a.out[(long long)b * a.out_stride + r] = a.out_scale ? t * a.out_scale[r] : t;
         }
     }
+    }
     if (!a.fin.enabled) return;
     // Fused finalisation: the CTA that completes the last block of a row tile
     // (counted in rows, across launches of the same frame) finalises it.
@@ -816,8 +847,8 @@ __device__ __forceinline__ void gemv_body(const GemvArgs& a) {
         const int rows_here = min(r0 + kGemvWarps * RPW, a.na) - r0;
         const int ft_rows = min(kFinRows, a.na - ft * kFinRows);
         fence_acq_rel_gpu();
-        const unsigned prev = atomicAdd(&a.fin.counters[ft], (unsigned)rows_here);
-        const bool last = prev + rows_here == (unsigned)(a.fin.nblk * ft_rows);
+        const unsigned prev = atomicAdd(&a.fin.counters[ft], (unsigned)(rows_here * (g1 - g0)));
+        const bool last = prev + rows_here * (g1 - g0) == (unsigned)(a.fin.nblk * ft_rows);
         if (last) fence_acq_rel_gpu();
         s_last = last;
     }
@@ -841,9 +872,20 @@ __device__ __forceinline__ void gemv_body(const GemvArgs& a) {
     }
 }
 
-template <int DT, int U, int RI, int RPW, bool kGated>
+template <int DT, int U, int RI, int RPW, bool kGated, int kGroup>
 __global__ void __launch_bounds__(kGemvWarps * 32) gemv_kernel(const __grid_constant__ GemvArgs a) {
-    gemv_body<DT, U, RI, RPW, kGated>(a);
+    gemv_body<DT, U, RI, RPW, kGated, kGroup>(a);
+}
+
+// Several column blocks per CTA, held to the resident CTAs per SM of the one-block
+// kernel (the loop over blocks costs it registers otherwise).
+template <int DT> struct GroupedMinCtas { static constexpr int value = 8; };
+template <> struct GroupedMinCtas<RTC_BF16> { static constexpr int value = 4; };
+template <> struct GroupedMinCtas<RTC_E4M3> { static constexpr int value = 5; };
+template <int DT, int U, int RI, int RPW, bool kGated, int kGroup>
+__global__ void __launch_bounds__(kGemvWarps * 32, GroupedMinCtas<DT>::value)
+    gemv_kernel_grouped(const __grid_constant__ GemvArgs a) {
+    gemv_body<DT, U, RI, RPW, kGated, kGroup>(a);
 }
 
 // One row per warp: the launches over a single column block (the POLC product, a
@@ -851,7 +893,7 @@ __global__ void __launch_bounds__(kGemvWarps * 32) gemv_kernel(const __grid_cons
 // them fit in one wave of eight CTAs per SM.
 template <int DT, int U, int RI, bool kGated>
 __global__ void __launch_bounds__(kGemvWarps * 32, 8) gemv_kernel_1row(const __grid_constant__ GemvArgs a) {
-    gemv_body<DT, U, RI, RI, kGated>(a);
+    gemv_body<DT, U, RI, RI, kGated, 1>(a);
 }
 
 // Telemetry entry of one frame: grid.y enumerates the recorded sections (one
@@ -962,23 +1004,33 @@ cudaError_t launch_gemv_t(const GemvArgs& base, int nb, long long avg_row_bytes,
     if (kNoRpw2 && rpw == 2) rpw = 1;
     GemvArgs a = base;
     a.tiles = (na + kGemvWarps * rpw - 1) / (kGemvWarps * rpw);
-    const dim3 grid((unsigned)(a.tiles * nb));
+    // consecutive column blocks per CTA, as many as keep that many waves
+    constexpr int kMaxGroup = DT == RTC_F32 ? RTC_GEMV_GROUP_F32 : DT == RTC_BF16 ? RTC_GEMV_GROUP_BF16 : RTC_GEMV_GROUP_E4M3;
+    // (one grouped instance, kMaxGroup, used when four rows per warp keep that many waves with it)
+    a.group = 1;
+    if (kMaxGroup > 1 && rpw >= 4 &&
+        (long long)a.tiles * ((nb + kMaxGroup - 1) / kMaxGroup) >= RTC_GEMV_GROUP_MIN_WAVES * 8LL * 152)
+        a.group = kMaxGroup;
+    const dim3 grid((unsigned)(a.tiles * ((nb + a.group - 1) / a.group)));
     // prefetch while waiting for the producer: about 96 MB, below the L2 size
-    const long long tile_bytes = std::max(1LL, avg_row_bytes * kGemvWarps * rpw);
+    const long long tile_bytes = std::max(1LL, avg_row_bytes * kGemvWarps * rpw * a.group);
     a.prefetch_ctas = pdl ? (int)std::min<long long>(grid.x, (96LL << 20) / tile_bytes) : 0;
-    if (rpw >= 4) return launch_maybe_pdl(gemv_kernel<DT, U, RI, (RI > 4 ? RI : 4), kG>, grid, a, pdl, st);
+    if constexpr (kMaxGroup > 1)
+        if (rpw >= 4 && a.group == kMaxGroup)
+            return launch_maybe_pdl(gemv_kernel_grouped<DT, U, RI, (RI > 4 ? RI : 4), kG, kMaxGroup>, grid, a, pdl, st);
+    if (rpw >= 4) return launch_maybe_pdl(gemv_kernel<DT, U, RI, (RI > 4 ? RI : 4), kG, 1>, grid, a, pdl, st);
     if constexpr (!kNoRpw2)
-        if (rpw >= 2) return launch_maybe_pdl(gemv_kernel<DT, U, RI, (RI > 2 ? RI : 2), kG>, grid, a, pdl, st);
+        if (rpw >= 2) return launch_maybe_pdl(gemv_kernel<DT, U, RI, (RI > 2 ? RI : 2), kG, 1>, grid, a, pdl, st);
     if constexpr (RI == 1) return launch_maybe_pdl(gemv_kernel_1row<DT, U, 1, kG>, grid, a, pdl, st);
-    else return launch_maybe_pdl(gemv_kernel<DT, U, RI, RI, kG>, grid, a, pdl, st);
+    else return launch_maybe_pdl(gemv_kernel<DT, U, RI, RI, kG, 1>, grid, a, pdl, st);
 }
 
 cudaError_t launch_gemv(int dtype, const void* M, const BlockDev* blocks, int b0, int nb, int na, const float* x,
                         const float* out_scale, float* out, long long out_stride, const FinaliseArgs* fin,
                         long long avg_row_bytes, bool pdl, cudaStream_t st, const int* gate_state) {
     if (nb <= 0 || na <= 0) return cudaSuccess;
-    GemvArgs a{static_cast<const uint8_t*>(M), blocks, b0, 0, na, x, out_scale, out, out_stride, FinaliseArgs{}, 0,
-               gate_state};
+    GemvArgs a{static_cast<const uint8_t*>(M), blocks, b0, nb, 0, na, x, out_scale, out, out_stride, FinaliseArgs{}, 0,
+               gate_state, 1};
     if (fin) a.fin = *fin;
     if (gate_state) {
         switch (dtype) {

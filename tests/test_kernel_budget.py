@@ -16,13 +16,16 @@ SRC = os.path.join(ROOT, "paper_1903_01852_gb300", "csrc", "rtc_kernels.cu")
 
 # mangled entry -> (what, register budget, spill budget in bytes)
 BUDGET = {
-    "_ZN3rtc11gemv_kernelILi0ELi4ELi1ELi4ELb0EEEvNS_8GemvArgsE": ("float32 MVM, 4 rows per warp", 32, 0),
+    "_ZN3rtc11gemv_kernelILi0ELi4ELi1ELi4ELb0ELi1EEEvNS_8GemvArgsE": ("float32 MVM, 4 rows per warp", 32, 0),
     # one row per warp (single-block launches: the POLC product, a row chunk's block, and every
     # float32 launch too small for four rows per warp): held to 32 registers so that their ~1000
     # CTAs fit one wave (no spill with packed float32 sums; a few bytes allowed)
     "_ZN3rtc16gemv_kernel_1rowILi0ELi4ELi1ELb0EEEvNS_8GemvArgsE": ("float32 MVM, 1 row per warp", 32, 32),
-    "_ZN3rtc11gemv_kernelILi1ELi2ELi4ELi4ELb0EEEvNS_8GemvArgsE": ("BF16 MVM", 64, 0),
-    "_ZN3rtc11gemv_kernelILi2ELi1ELi4ELi4ELb0EEEvNS_8GemvArgsE": ("E4M3 MVM", 48, 0),
+    "_ZN3rtc11gemv_kernelILi1ELi2ELi4ELi4ELb0ELi1EEEvNS_8GemvArgsE": ("BF16 MVM", 64, 0),
+    "_ZN3rtc11gemv_kernelILi2ELi1ELi4ELi4ELb0ELi1EEEvNS_8GemvArgsE": ("E4M3 MVM", 48, 0),
+    # two column blocks per CTA (whole-frame BF16 / E4M3 launches), held to the one-block kernels' CTAs per SM
+    "_ZN3rtc19gemv_kernel_groupedILi1ELi2ELi4ELi4ELb0ELi2EEEvNS_8GemvArgsE": ("BF16 MVM, two blocks per CTA", 64, 0),
+    "_ZN3rtc19gemv_kernel_groupedILi2ELi1ELi4ELi4ELb0ELi2EEEvNS_8GemvArgsE": ("E4M3 MVM, two blocks per CTA", 48, 0),
     # a pre-enqueued chunk's MVM (its mailbox checked after the wait for the slopes); a chunk's
     # launches are small enough to take one row per warp
     "_ZN3rtc16gemv_kernel_1rowILi0ELi4ELi1ELb1EEEvNS_8GemvArgsE": ("float32 MVM, 1 row per warp, pre-enqueued",
