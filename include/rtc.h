@@ -275,9 +275,11 @@ typedef struct rtc_chunk {
  * ran out first, they gave up the same way.  Both cases fall back to ordinary
  * launches, with the same results.  rtc_get_info counts the three outcomes.
  * While kernels wait, anything that waits for all work on the device
- * (cudaDeviceSynchronize, cudaFree, another loop's rtc_destroy) waits for them
- * too: until their chunk arrives, the frame is dropped or the loop destroyed,
- * or the wait runs out. */
+ * (cudaDeviceSynchronize, cudaFree, another loop's rtc_destroy), and this
+ * loop's own rtc_sync, rtc_get_state, rtc_set_state, rtc_check_guards and
+ * rtc_set_partial_output called in the middle of a frame, wait for them too:
+ * until their chunk arrives, the frame is dropped or the loop destroyed, or
+ * the wait runs out (and the chunk then takes ordinary launches). */
 int rtc_submit_pixels(rtc_loop* loop, const rtc_chunk* chunk);
 
 /* Several chunks in one call (no counterpart in the paper; for a host that
