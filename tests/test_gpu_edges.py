@@ -230,3 +230,53 @@ def test_lowest_stream_priority_gives_the_same_commands(rtc, torch_cuda):
             low.submit_frame(k + 1, f)
             high.submit_frame(k + 1, f)
             assert np.array_equal(low.get_commands(timeout_us=WAIT_US)[1], high.get_commands(timeout_us=WAIT_US)[1])
+
+
+GROUPED_SCRIPT = textwrap.dedent("""
+    import sys, numpy as np
+    sys.path.insert(0, "tests")
+    from oracle import quantize_rows
+    from paper_1903_01852_gb300 import binding as rtc, synth
+    from parity_util import device_frames
+    from test_gpu_parity import ragged_config
+    out = {}
+    for fmt in ("f32", "bf16", "e4m3"):
+        cfg = ragged_config(seed=281)
+        if fmt != "f32":
+            codes, scale = quantize_rows(cfg["M"], fmt)
+            pc, ps = quantize_rows(cfg["P"], fmt)
+            cfg.update(M=codes, M_scale=scale, M_dtype=fmt, P=pc, P_scale=ps, P_dtype=fmt)
+        frames = synth.draw_frames(cfg, 3, seed=282)
+        with rtc.Loop(cfg) as whole, rtc.Loop(cfg) as chunked:
+            for k, f in enumerate(frames):
+                whole.process_frame(k + 1, device_frames(f))
+                chunked.submit_frame(k + 1, f, [synth.chunk_plan(w, 3) for w in cfg["wfs"]])
+                out[f"{fmt}_whole_{k}"] = whole.get_commands(timeout_us=30_000_000)[1]
+                out[f"{fmt}_chunked_{k}"] = chunked.get_commands(timeout_us=30_000_000)[1]
+    np.savez(sys.argv[1], **out)
+""")
+
+
+def test_grouped_mvm_gives_the_bits_of_one_block_per_cta(torch_cuda, tmp_path):
+    # A build whose MVM CTAs always take several consecutive column blocks (2 for
+    # float32, 3 for BF16, 4 for E4M3; the last group of a launch shorter) against
+    # the default build, on a ragged loop submitted whole and in row chunks: the
+    # per-block sums and the finalisation are the same, so the commands are too.
+    from paper_1903_01852_gb300.build import build
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    lib = build(defines=["RTC_GEMV_GROUP_MIN_WAVES=0", "RTC_GEMV_GROUP_F32=2", "RTC_GEMV_GROUP_BF16=3",
+                         "RTC_GEMV_GROUP_E4M3=4", "RTC_GEMV_MIN_WAVES=0"], out=str(tmp_path / "librtc.so"))
+    res = {}
+    for name, env_lib in (("grouped", lib), ("default", None)):
+        env = dict(os.environ, PYTHONPATH=root + os.pathsep + os.environ.get("PYTHONPATH", ""))
+        env.pop("RTC_LIBRARY", None)
+        if env_lib:
+            env["RTC_LIBRARY"] = env_lib
+        path = str(tmp_path / f"{name}.npz")
+        r = subprocess.run([sys.executable, "-c", GROUPED_SCRIPT, path], env=env, capture_output=True, text=True,
+                           timeout=600, cwd=root)
+        assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-3000:]
+        res[name] = dict(np.load(path))
+    assert res["grouped"].keys() == res["default"].keys() and len(res["default"]) == 18
+    for k in res["default"]:
+        assert np.array_equal(res["grouped"][k], res["default"][k]), k
