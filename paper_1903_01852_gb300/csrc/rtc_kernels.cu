@@ -579,6 +579,15 @@ __device__ __forceinline__ uint4 ld_stream(const uint4* p) {
 __device__ __forceinline__ float bf_lo(uint32_t u) { return __uint_as_float(u << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
 
+// Vectors per lane of the single-block BF16 / E4M3 products without finalisation
+// (0: the MVM kernel).  E4M3 POLC, MCAO 26.6 -> 18.4 us, LTAO 20.4 -> 14.3 us (the
+// same with 4); BF16 unchanged at 2 or 4 (24.5 us: 235 CTAs over 152 SMs), so off.
+#ifndef RTC_GEMV_BF16_U_DEEP
+#define RTC_GEMV_BF16_U_DEEP 0
+#endif
+#ifndef RTC_GEMV_E4M3_U_DEEP
+#define RTC_GEMV_E4M3_U_DEEP 2
+#endif
 #ifndef RTC_GEMV_GROUP_MIN_WAVES
 #define RTC_GEMV_GROUP_MIN_WAVES 2 // waves of 8 CTAs per SM a grouped launch keeps at least
 #endif
@@ -888,6 +897,14 @@ __global__ void __launch_bounds__(kGemvWarps * 32, GroupedMinCtas<DT>::value)
     gemv_body<DT, U, RI, RPW, kGated, kGroup>(a);
 }
 
+// A narrow format's single-block product without finalisation (the POLC product
+// P a, or D a): its few hundred CTAs hold under two per SM whatever their
+// registers, so each lane keeps more vectors in flight than the MVM kernels can.
+template <int DT, int U, int RI, bool kGated>
+__global__ void __launch_bounds__(kGemvWarps * 32, 2) gemv_kernel_deep(const __grid_constant__ GemvArgs a) {
+    gemv_body<DT, U, RI, RI, kGated, 1>(a);
+}
+
 // One row per warp: the launches over a single column block (the POLC product, a
 // row chunk's block) have about a thousand CTAs, and at <= 32 registers all of
 // them fit in one wave of eight CTAs per SM.
@@ -1004,6 +1021,14 @@ cudaError_t launch_gemv_t(const GemvArgs& base, int nb, long long avg_row_bytes,
     if (kNoRpw2 && rpw == 2) rpw = 1;
     GemvArgs a = base;
     a.tiles = (na + kGemvWarps * rpw - 1) / (kGemvWarps * rpw);
+    constexpr int kUDeep = DT == RTC_BF16 ? RTC_GEMV_BF16_U_DEEP : DT == RTC_E4M3 ? RTC_GEMV_E4M3_U_DEEP : 0;
+    if constexpr (kUDeep > 0 && RI == 4) {
+        if (!a.fin.enabled && nb == 1 && rpw == RI && a.tiles <= 2 * 152) {
+            const long long tile_bytes = std::max(1LL, avg_row_bytes * kGemvWarps * rpw);
+            a.prefetch_ctas = pdl ? (int)std::min<long long>(a.tiles, (96LL << 20) / tile_bytes) : 0;
+            return launch_maybe_pdl(gemv_kernel_deep<DT, kUDeep, RI, kG>, dim3((unsigned)a.tiles), a, pdl, st);
+        }
+    }
     // consecutive column blocks per CTA, as many as keep that many waves
     constexpr int kMaxGroup = DT == RTC_F32 ? RTC_GEMV_GROUP_F32 : DT == RTC_BF16 ? RTC_GEMV_GROUP_BF16 : RTC_GEMV_GROUP_E4M3;
     // (one grouped instance, kMaxGroup, used when four rows per warp keep that many waves with it)

@@ -26,6 +26,8 @@ BUDGET = {
     # two column blocks per CTA (whole-frame BF16 / E4M3 launches), held to the one-block kernels' CTAs per SM
     "_ZN3rtc19gemv_kernel_groupedILi1ELi2ELi4ELi4ELb0ELi2EEEvNS_8GemvArgsE": ("BF16 MVM, two blocks per CTA", 64, 0),
     "_ZN3rtc19gemv_kernel_groupedILi2ELi1ELi4ELi4ELb0ELi2EEEvNS_8GemvArgsE": ("E4M3 MVM, two blocks per CTA", 48, 0),
+    # the single-block E4M3 product without finalisation (POLC): two vectors per lane, two CTAs per SM
+    "_ZN3rtc16gemv_kernel_deepILi2ELi2ELi4ELb0EEEvNS_8GemvArgsE": ("E4M3 POLC product", 128, 0),
     # a pre-enqueued chunk's MVM (its mailbox checked after the wait for the slopes); a chunk's
     # launches are small enough to take one row per warp
     "_ZN3rtc16gemv_kernel_1rowILi0ELi4ELi1ELb1EEEvNS_8GemvArgsE": ("float32 MVM, 1 row per warp, pre-enqueued",
