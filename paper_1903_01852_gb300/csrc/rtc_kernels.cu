@@ -101,10 +101,11 @@ __device__ __forceinline__ void store_pair(float* __restrict__ s_pad, int pad, c
 // column sums, so they are not a dependent load at the end.
 // kAllRows (row chunks read in place over the CPU-GPU link, whose latency is
 // several times that of HBM): a thread first issues the loads of all its pixel
-// rows (up to kRowsInFlight), then calibrates them four rows at a time; the
-// additions keep the same order, so the slopes are bit-identical to the other
-// variant.  It takes ~160 registers (one CTA per SM): right for a chunk's few
-// dozen CTAs, not for a whole frame's hundreds.
+// rows (up to kRowsInFlight) and of their dark and flat maps, then calibrates
+// them; the additions keep the same order, so the slopes are bit-identical to the
+// other variant.  It takes ~220 registers (one CTA per SM): right for a chunk's
+// few dozen CTAs, not for a whole frame's hundreds.  (Calibration loads in three
+// dependent batches of four rows instead: paced latency 1-2 us longer.)
 constexpr int kRowsInFlight = 12;
 
 template <bool kAllRows>
@@ -147,38 +148,32 @@ __device__ void sh_part(const SlopePart& P, const SlopeRow& row, const WfsDev& W
         float Y[4] = {0.f, 0.f, 0.f, 0.f};
         int r = P.pr0 + g;
         if constexpr (kAllRows) {
+            // every row's pixel and calibration loads issued before the first is used
             uint2 rw[kRowsInFlight];
+            float4 d[kRowsInFlight], f[kRowsInFlight];
 #pragma unroll
             for (int j = 0; j < kRowsInFlight; ++j) {
                 const int rr = r + j * G;
-                if (rr < P.pr1)
-                    rw[j] = __ldg(reinterpret_cast<const uint2*>(px + ((long long)y0 + rr - prow0) * pitch + xa));
+                if (rr < P.pr1) {
+                    const long long yy = y0 + rr;
+                    rw[j] = __ldg(reinterpret_cast<const uint2*>(px + (yy - prow0) * pitch + xa));
+                    d[j] = __ldg(reinterpret_cast<const float4*>(W.dark + yy * W.calib_pitch + xa));
+                    f[j] = __ldg(reinterpret_cast<const float4*>(W.flat + yy * W.calib_pitch + xa));
+                }
             }
 #pragma unroll
-            for (int j0 = 0; j0 < kRowsInFlight; j0 += 4) {
-                float4 d[4], f[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const long long yy = y0 + r + (j0 + k) * G;
-                    if (r + (j0 + k) * G < P.pr1) {
-                        d[k] = __ldg(reinterpret_cast<const float4*>(W.dark + yy * W.calib_pitch + xa));
-                        f[k] = __ldg(reinterpret_cast<const float4*>(W.flat + yy * W.calib_pitch + xa));
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int rr = r + (j0 + k) * G;
-                    if (rr < P.pr1) {
-                        const uint2 q2 = rw[j0 + k];
-                        const float yc = float(rr) - half;
-                        const float t0 = calibrate(q2.x & 0xffffu, d[k].x, f[k].x, T, mode);
-                        const float t1 = calibrate(q2.x >> 16, d[k].y, f[k].y, T, mode);
-                        const float t2 = calibrate(q2.y & 0xffffu, d[k].z, f[k].z, T, mode);
-                        const float t3 = calibrate(q2.y >> 16, d[k].w, f[k].w, T, mode);
-                        F[0] += t0; F[1] += t1; F[2] += t2; F[3] += t3;
-                        Y[0] = fmaf(t0, yc, Y[0]); Y[1] = fmaf(t1, yc, Y[1]);
-                        Y[2] = fmaf(t2, yc, Y[2]); Y[3] = fmaf(t3, yc, Y[3]);
-                    }
+            for (int j = 0; j < kRowsInFlight; ++j) {
+                const int rr = r + j * G;
+                if (rr < P.pr1) {
+                    const uint2 q2 = rw[j];
+                    const float yc = float(rr) - half;
+                    const float t0 = calibrate(q2.x & 0xffffu, d[j].x, f[j].x, T, mode);
+                    const float t1 = calibrate(q2.x >> 16, d[j].y, f[j].y, T, mode);
+                    const float t2 = calibrate(q2.y & 0xffffu, d[j].z, f[j].z, T, mode);
+                    const float t3 = calibrate(q2.y >> 16, d[j].w, f[j].w, T, mode);
+                    F[0] += t0; F[1] += t1; F[2] += t2; F[3] += t3;
+                    Y[0] = fmaf(t0, yc, Y[0]); Y[1] = fmaf(t1, yc, Y[1]);
+                    Y[2] = fmaf(t2, yc, Y[2]); Y[3] = fmaf(t3, yc, Y[3]);
                 }
             }
             r += kRowsInFlight * G;    // rows beyond (never with the default part split) go below

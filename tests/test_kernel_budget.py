@@ -33,13 +33,12 @@ BUDGET = {
     "_ZN3rtc16gemv_kernel_1rowILi0ELi4ELi1ELb1EEEvNS_8GemvArgsE": ("float32 MVM, 1 row per warp, pre-enqueued",
                                                                   32, 32),
     "_ZN3rtc13slopes_kernelILb0ELb0EEEvNS_9SlopeArgsE": ("slope kernel", 64, 0),
-    # pixels read over the CPU-GPU link: every pixel row of a thread in flight at once (launched for
-    # row chunks and page-locked frames, where a few CTAs per SM are enough)
-    "_ZN3rtc13slopes_kernelILb1ELb0EEEvNS_9SlopeArgsE": ("slope kernel, host pixels", 168, 0),
-    # pre-enqueued chunks (launched behind the one-warp gate kernel); the host-pixel one is compiled to
-    # 128 registers with a word or two spilled
+    # pixels read over the CPU-GPU link: every pixel row of a thread and its calibration in flight at
+    # once (launched for row chunks, a few dozen CTAs: one per SM is enough)
+    "_ZN3rtc13slopes_kernelILb1ELb0EEEvNS_9SlopeArgsE": ("slope kernel, host pixels", 232, 0),
+    # pre-enqueued chunks (launched behind the one-warp gate kernel)
     "_ZN3rtc13slopes_kernelILb0ELb1EEEvNS_9SlopeArgsE": ("slope kernel, pre-enqueued", 64, 0),
-    "_ZN3rtc13slopes_kernelILb1ELb1EEEvNS_9SlopeArgsE": ("slope kernel, host pixels, pre-enqueued", 168, 16),
+    "_ZN3rtc13slopes_kernelILb1ELb1EEEvNS_9SlopeArgsE": ("slope kernel, host pixels, pre-enqueued", 232, 0),
 }
 
 
