@@ -280,3 +280,33 @@ def test_prelaunch_in_a_shard_loop(rtc, torch_cuda):
             a, b = pre.get_commands(timeout_us=WAIT_US)[1], plain.get_commands(timeout_us=WAIT_US)[1]
             assert np.array_equal(a, b)
         assert pre.info()["prelaunch_used"] == expected_prelaunches(cfg, plans, len(frames) - 1)
+
+
+def test_a_batch_that_starts_a_new_frame_drops_the_incomplete_one(rtc, torch_cuda):
+    import ctypes as C
+    cfg = dict(sh_loop(seed=581), prelaunch_wait_us=1_000_000)
+    frames = synth.draw_frames(cfg, 3, seed=582)
+    plans = [synth.chunk_plan(w, 3) for w in cfg["wfs"]]
+    bufs = in_place_buffers(torch_cuda, frames, "host")
+    n = max(len(p) for p in plans)
+    rounds = lambda k, fid: [rtc.Loop.chunks(fid, [(w, *p[c], bufs[k][w][p[c][0]:p[c][1]])
+                                                   for w, p in enumerate(plans) if c < len(p)]) for c in range(n)]
+    with rtc.Loop(cfg, prelaunch=True) as pre, rtc.Loop(cfg) as plain:
+        for lp in (pre, plain):
+            for arr in rounds(0, 1):
+                assert lp.submit_chunks(arr) == rtc.RTC_OK
+            lp.get_commands(timeout_us=WAIT_US)
+            assert lp.submit_chunks(rounds(1, 2)[0]) == rtc.RTC_OK        # frame 2: first round only
+        # frame 3's first round drops frame 2 and is accepted whole
+        for lp in (pre, plain):
+            arr = rounds(2, 3)[0]
+            acc = C.c_int32(-1)
+            assert rtc.lib.rtc_submit_pixels_n(lp._h, arr, len(arr), C.byref(acc)) == rtc.RTC_EDROPPED
+            assert acc.value == len(arr)
+            for arr in rounds(2, 3)[1:]:
+                assert lp.submit_chunks(arr) == rtc.RTC_OK
+        a, b = pre.get_commands(timeout_us=WAIT_US), plain.get_commands(timeout_us=WAIT_US)
+        assert a[0] == b[0] == 3 and np.array_equal(a[1], b[1])
+        info = pre.info()
+        nsh = sum(1 for w in cfg["wfs"] if w["kind"] == "sh")
+        assert info["frames_dropped"] == 1 and info["prelaunch_cancelled"] == nsh and info["prelaunch_expired"] == 0
