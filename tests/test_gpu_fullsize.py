@@ -89,16 +89,19 @@ def test_full_size_mcao_e4m3_device_frames(rtc, torch_cuda, mcao):
     print("mcao e4m3 (slopes, commands) vs the stored matrix:", errs)
 
 
-def test_full_size_mcao_fp32_row_chunks_read_in_place(rtc, torch_cuda, mcao):
+@pytest.mark.parametrize("prelaunch", [False, True])
+def test_full_size_mcao_fp32_row_chunks_read_in_place(rtc, torch_cuda, mcao, prelaunch):
     # The camera-paced path: each LGS frame in 8 row chunks of whole subaperture
     # rows, each NGS frame in one, submitted from page-locked host memory and
-    # read in place; same bits as whole frames in HBM, and the oracle's commands.
+    # read in place (with prelaunch, each LGS chunk after the first of a frame
+    # through kernels enqueued before it arrived); same bits as whole frames in
+    # HBM, and the oracle's commands.
     torch = torch_cuda
     cfg, frames = mcao
     plans = [synth.chunk_plan(w, 8 if w["nsubx"] > 2 else 1) for w in cfg["wfs"]]
     host = pinned_frames(torch, frames)
     ref = OracleLoop(cfg)
-    with rtc.Loop(cfg, telemetry=True) as chunked, rtc.Loop(cfg, telemetry=True) as whole:
+    with rtc.Loop(cfg, telemetry=True, prelaunch=prelaunch) as chunked, rtc.Loop(cfg, telemetry=True) as whole:
         for k, f in enumerate(frames):
             for w, (plan, x) in enumerate(zip(plans, host[k])):
                 for r0, r1 in plan:
@@ -111,6 +114,13 @@ def test_full_size_mcao_fp32_row_chunks_read_in_place(rtc, torch_cuda, mcao):
             s_ref, a_ref = ref.step(f)
             assert rel(s, s_ref) <= TOL_F32 and rel(a, a_ref) <= TOL_F32
         assert chunked.check_guards() == 0 and whole.check_guards() == 0
+        if prelaunch:
+            # submitted back to back, a camera can run ahead of the GPU by more chunks than it
+            # has mailboxes (four): such a chunk takes ordinary launches (none is cancelled)
+            lgs = sum(1 for w in cfg["wfs"] if w["nsubx"] > 2)
+            info = chunked.info()
+            assert 0 < info["prelaunch_used"] <= (len(frames) - 1) * lgs * 7
+            assert info["prelaunch_cancelled"] == 0 and info["prelaunch_expired"] == 0
 
 
 def test_full_size_serving_mix_each_loop_against_its_oracle(rtc, torch_cuda):
