@@ -274,6 +274,10 @@ typedef struct rtc_chunk {
  * destroyed) the mailbox is cancelled and the kernels do nothing; if the wait
  * ran out first, they gave up the same way.  Both cases fall back to ordinary
  * launches, with the same results.  rtc_get_info counts the three outcomes.
+ * Nothing is enqueued ahead for a chunk the previous frame did not have (or
+ * copied), for one that completes no subaperture row, or while four earlier
+ * pre-enqueued chunks of the same camera still have kernels running (a host
+ * that runs ahead of the GPU): such a chunk takes ordinary launches.
  * While kernels wait, anything that waits for all work on the device
  * (cudaDeviceSynchronize, cudaFree, another loop's rtc_destroy), and this
  * loop's own rtc_sync, rtc_get_state, rtc_set_state, rtc_check_guards and
