@@ -744,7 +744,11 @@ def format_errors(args, frames, rtc, dev_frames, local, nframes=100):
 
 
 def quick_arm(args, cfg, frames, rtc, torch, local):
-    """Profiling aid: only the unpaced, HBM-resident float32 loop on the chosen workload."""
+    """Profiling aid: only the unpaced, HBM-resident float32 loop on the chosen workload
+    (--chunked: the frames submitted instead as rounds of row chunks, 8 per camera with more
+    than 2x2 subapertures, from page-locked memory read in place, unpaced, ordinary launches)."""
+    if args.chunked:
+        return quick_chunked(args, cfg, frames, rtc, torch, local)
     dev_frames = []
     for f in frames:
         per = []
@@ -770,6 +774,25 @@ def quick_arm(args, cfg, frames, rtc, torch, local):
     print(json.dumps({"workload": args.workload, "quick": True, "dtype": args.dtype, "latency_us": lat,
                       "slopes_us": sl, "polc_us": po, "mvm_us": mvm, "errors": errors,
                       "mvm_gbs": mvm_bytes(info, cfg) / (mvm * 1e-6) / 1e9}), flush=True)
+
+
+def quick_chunked(args, cfg, frames, rtc, torch, local):
+    from paper_1903_01852_gb300 import synth
+    host = []
+    for f in frames:
+        per = []
+        for x in f:
+            h, w = x.shape
+            t = torch.zeros((h, (w + 7) // 8 * 8), dtype=torch.int16, pin_memory=True)
+            t.numpy()[:, :w] = x.view(np.int16)
+            per.append(t[:, :w])
+        host.append(per)
+    plans = [synth.chunk_plan(w, NCHUNKS if w.get("nsubx", 0) > 2 else 1) for w in cfg["wfs"]]
+    sampler = ClockSampler(local)
+    with rtc.Loop(cfg, device=local, telemetry=True) as loop:
+        lat, _ = run_host_path(loop, host, plans, args.steps, args.warmup, sampler, 1, paced=False)
+    print(json.dumps({"workload": args.workload, "quick": True, "chunked": True, "dtype": args.dtype,
+                      "latency_us": stats(lat)}), flush=True)
 
 
 SERVING_LOOPS = (("ltao", "ltao", 500.0), ("mcao", "mcao", 500.0), ("scao_a", "elt_scao_sh", 1000.0),
@@ -1055,6 +1078,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="profiling aid: only the unpaced loop")
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "e4m3"], help="matrix storage for --quick")
     ap.add_argument("--errors", action="store_true", help="--quick: also errors against the FP64 oracle")
+    ap.add_argument("--chunked", action="store_true", help="--quick: rounds of row chunks from page-locked memory")
     ap.add_argument("--error-frames", type=int, default=100, help="--errors: frames compared with the oracle")
     args = ap.parse_args()
     if args.warmup < 3:
