@@ -310,3 +310,25 @@ def test_a_batch_that_starts_a_new_frame_drops_the_incomplete_one(rtc, torch_cud
         info = pre.info()
         nsh = sum(1 for w in cfg["wfs"] if w["kind"] == "sh")
         assert info["frames_dropped"] == 1 and info["prelaunch_cancelled"] == nsh and info["prelaunch_expired"] == 0
+
+
+def test_prelaunch_with_explicit_polc(rtc, torch_cuda):
+    # explicit POLC: the slope kernel adds u = D a to every slope, the pre-enqueued one too
+    cfg = sh_loop(seed=591)
+    rng = np.random.default_rng(592)
+    cfg = dict(cfg, P=None, P_scale=None, polc="explicit",
+               D=synth.interaction_matrix(rng, cfg["ns"], cfg["na"], m_sd=1e-2))   # M is N(0, 1e-4) here
+    frames = synth.draw_frames(cfg, 4, seed=593)
+    plans = [synth.chunk_plan(w, 4) for w in cfg["wfs"]]
+    bufs = in_place_buffers(torch_cuda, frames, "host")
+    ref = OracleLoop(cfg)
+    with rtc.Loop(cfg, telemetry=True, prelaunch=True) as pre, rtc.Loop(cfg, telemetry=True) as plain:
+        for k, f in enumerate(frames):
+            submit(pre, k + 1, bufs[k], plans)
+            submit(plain, k + 1, bufs[k], plans)
+            (fa, a), (fb, b) = pre.get_commands(timeout_us=WAIT_US), plain.get_commands(timeout_us=WAIT_US)
+            sa, sb = pre.get_telemetry(fa, timeout_us=WAIT_US)[0], plain.get_telemetry(fb, timeout_us=WAIT_US)[0]
+            assert np.array_equal(a, b) and np.array_equal(sa, sb)
+            s_ref, a_ref = ref.step(f)
+            assert rel(sa, s_ref) <= TOL_F32 and rel(a, a_ref) <= TOL_F32
+        assert pre.info()["prelaunch_used"] == expected_prelaunches(cfg, plans, len(frames) - 1)
